@@ -1,0 +1,188 @@
+/*
+ * pgc.h -- C ABI of the GB300 (sm_103a) particle stochastic-Galerkin solver for the
+ * space-homogeneous semiclassical Boltzmann equation of electrons in a graphene nanoribbon
+ * (Medaglia, Nastasi, Romano, Zanella, "Uncertainty quantification for charge transport in GNRs
+ * through particle Galerkin methods for the semiclassical Boltzmann equation", arXiv:2404.19602).
+ *
+ * What one call computes
+ * ----------------------
+ * The ensemble is N particles.  Particle i carries its wave-vector as gPC coefficients
+ * khat_{i,h}, h = 0..P-1 (Eq. (23)); with deterministic inputs P = 1 and khat is k itself.
+ * pgc_step advances every particle by n_steps time steps of the Lie splitting of Sec. 3:
+ *   1. field drift khat_{x,h} -= (e/hbar) dt int E(z) Psi_h p dz  (Eq. (17), Sec. 4.1);
+ *   2. DSMC collision loop of Algorithm 1 (deterministic) / Algorithm 2 (stochastic Galerkin):
+ *      free flight dt = -ln(xi) / max_z Gamma_tot(z) (Eqs. (18),(19),(25)), mechanism
+ *      selection over the rate vector of Eq. (20), final states h^1..h^7 of Sec. 3, Pauli
+ *      acceptance against the previous-step histogram (Eqs. (22),(27)), projection onto the
+ *      gPC basis (Eqs. (28)-(30));
+ *   3. the histogram f^{n+1}_{N,rl}(z_q) of Eq. (24) at the quadrature nodes, and, every
+ *      moments_every steps, the observables of Eqs. (35)-(37) at the nodes and their mean and
+ *      variance over z (Sec. 4.2).
+ * Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter
+ * (i, stream_id, step, attempt); the same counters drive the FP64 CPU oracle of the tests.
+ *
+ * Readings of points the paper leaves open (the design notes list them with reasons):
+ *   - Gauss-Legendre quadrature with quad_per_dim nodes per random dimension for every z-integral;
+ *   - orthonormal Legendre basis sqrt(2h+1) P_h; in 2-D total degree <= M, graded order
+ *     h -> (degree in z1, degree in z2) = (t-j, j) for t = 0..M, j = 0..t;
+ *     z1 is the band-minimum variable, z2 the field variable; node q = q1 * quad_per_dim + q2;
+ *   - the majorant is the maximum over the nodes; the self-scattering entry of node q is
+ *     Gamma_tilde - sum_nu Gamma_nu(z_q);
+ *   - the flight time is drawn again after every collision; at most max_collisions per step;
+ *   - Pauli: f = N_rl / Nmax with Nmax the maximum of the initial histogram (default), the
+ *     histogram counted on the fixed grid before the drift and looked up at cell(k' + (e/hbar)E dt);
+ *   - the edge final angle is absolute; its CDF is the trapezoid CDF on n_theta_edge points.
+ *
+ * Units: energy eV, time fs, field V/cm, wave-vector nm^-1.  Velocities m/s, density m^-2,
+ * sheet current J = -e n V_x in A/m.
+ *
+ * Memory and ownership
+ * --------------------
+ * The caller owns every device buffer: it asks pgc_query_sizes for the byte counts, allocates
+ * them (e.g. as torch tensors), and passes the device pointers to pgc_init; they must stay valid
+ * until pgc_destroy.  The context owns only host-side tables.  Device layouts:
+ *   state   : R khat[2][P][ld], R = float (PGC_FP32) or double (PGC_FP64), c = x,y outermost,
+ *             ld = N rounded up to a multiple of 32; 256-byte aligned base required;
+ *   hist    : uint32 H[3][Q][Nk][Nk] (three rotating buffers; cell (r,l) of k is
+ *             r = floor((kx+Lk)/dk), l = floor((ky+Lk)/dk));
+ *   scratch : work space (collider queue, block partial sums, time series, counters).
+ * All calls on a context are ordered on the CUDA stream given to pgc_init; calls that return
+ * host data (pgc_moments, pgc_get_state, pgc_counters, pgc_reconstruct_f) synchronize it.
+ *
+ * Errors
+ * ------
+ * Every call returns a pgc_status and never throws across the ABI.  pgc_last_error(ctx) gives a
+ * message for the last failing call on ctx (pgc_last_error(NULL) for failures before a context
+ * exists).  A device-side error flag (e.g. a collision cap) is read back by pgc_counters.
+ * After PGC_ECUDA the context is unusable (PGC_ESTATE) and must be destroyed.
+ */
+#ifndef PGC_H
+#define PGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGC_OK = 0,
+    PGC_EINVAL = 1,          /* invalid argument or configuration */
+    PGC_ENOMEM = 2,          /* host allocation failed / buffer too small */
+    PGC_ECUDA = 3,           /* a CUDA runtime call failed */
+    PGC_ESTATE = 4,          /* context in a failed state */
+    PGC_ETIMEOUT = 5,        /* a bounded device wait gave up */
+    PGC_EUNSUPPORTED = 6     /* valid but not compiled (e.g. basis size without a kernel) */
+} pgc_status;
+
+/* mechanism bits, in the order of the rate vector Lambda of Eq. (20) */
+enum {
+    PGC_MECH_AC = 1, PGC_MECH_OPM = 2, PGC_MECH_OPP = 4, PGC_MECH_KM = 8, PGC_MECH_KP = 16,
+    PGC_MECH_EDGE = 32, PGC_MECH_ALL = 63
+};
+enum { PGC_FP32 = 0, PGC_FP64 = 1 };
+enum { PGC_PAULI_INITIAL_MAX = 0, PGC_PAULI_CURRENT_MAX = 1, PGC_PAULI_OFF = 2 };
+enum { PGC_FS_PAPER = 0, PGC_FS_EXACT_ENERGY = 1 };
+
+/* counters returned by pgc_counters */
+enum {
+    PGC_CNT_ATTEMPTS = 0,     /* collision events (real or self) */
+    PGC_CNT_CHANGED = 1,      /* events that changed the state at >= 1 node */
+    PGC_CNT_REJECTED = 2,     /* node-level Pauli rejections */
+    PGC_CNT_CAPPED = 3,       /* particle-steps that hit max_collisions */
+    PGC_CNT_OUT_OF_GRID = 4,  /* node values outside [-Lk,Lk]^2 in the last histogram */
+    PGC_CNT_QUEUED = 5,       /* particle-steps sent to the collider kernel */
+    PGC_CNT_ERROR = 6,        /* device error flag (0 = none) */
+    PGC_CNT_STEPS = 7,        /* time steps done */
+    PGC_NUM_COUNTERS = 8
+};
+
+typedef struct { double lo, hi; } pgc_interval;  /* lo == hi: deterministic input */
+
+typedef struct {
+    double T_K;              /* lattice and initial Fermi-Dirac temperature (300) */
+    double eps_F_eV;         /* Fermi level of the initial state (0.4) */
+    pgc_interval eps0_eV;    /* conduction-band minimum hbar vF pi / W; band gap E_g = 2 eps0 */
+    pgc_interval Ex_Vcm;     /* field along x; E_y = 0 */
+    uint32_t mech_mask;      /* PGC_MECH_*; 0 = ballistic */
+    double alpha;            /* self-scattering tuning of Eq. (19) (0.1) */
+    int32_t Nk;              /* grid cells per direction (240) */
+    double Lk_hvF_eV;        /* L_k * hbar vF (5) */
+    int32_t degree_M;        /* gPC degree (total degree in 2-D) */
+    int32_t quad_per_dim;    /* Gauss-Legendre nodes per random dimension (M + 1) */
+    int64_t n_particles;     /* N >= 1 */
+    double dt_fs;            /* time step (1) */
+    uint64_t seed;           /* Philox key */
+    uint32_t stream_id;      /* second Philox counter word (case / ensemble id) */
+    int32_t precision;       /* PGC_FP32 (state FP32, reductions FP64) or PGC_FP64 */
+    int32_t pauli_norm;      /* PGC_PAULI_* */
+    int32_t final_state;     /* PGC_FS_* */
+    int32_t n_theta_edge;    /* trapezoid points of the edge integral (64; even, 4..256) */
+    int32_t max_collisions;  /* per particle and step (32) */
+    int32_t max_outputs;     /* capacity of the moment time series */
+} pgc_config;
+
+typedef struct pgc_ctx pgc_ctx;
+
+/* Fill cfg with the defaults of Sec. 5 (300 K, eps_F 0.4 eV, eps0 0.1 eV, 5 kV/cm, all
+ * mechanisms, alpha 0.1, Nk 240, Lk hbar vF 5 eV, M 5, 6 nodes, N 1e4, 1 fs, seed 1, FP32). */
+void pgc_config_default(pgc_config *cfg);
+
+/* Validate cfg and report the device buffer sizes (bytes) and the basis / node counts.
+ * Any out pointer may be NULL.  Returns PGC_EINVAL / PGC_EUNSUPPORTED for a bad cfg. */
+pgc_status pgc_query_sizes(const pgc_config *cfg, size_t *state_bytes, size_t *hist_bytes,
+                           size_t *scratch_bytes, int32_t *P, int32_t *Q);
+
+/* Create a context on the current CUDA device and set up the initial state:
+ * if h_init_khat is NULL, particles are sampled on the device from the Fermi-Dirac state
+ * (Sec. 2) by the inverse CDF of eps*FD(eps) with one uniform shared by all z, and projected
+ * (Eq. (23)); otherwise h_init_khat (host, FP64, [2][P][N]) is uploaded.  Then the histogram
+ * f^0 and the moments at t = 0 are computed.  stream is a cudaStream_t (NULL = default).
+ * d_state / d_hist / d_scratch: caller-owned device buffers of the queried sizes. */
+pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_scratch,
+                    const double *h_init_khat, void *stream, pgc_ctx **out);
+
+/* Advance n_steps time steps (>= 0).  If moments_every > 0, the moments are recorded after
+ * every step whose index is a multiple of moments_every (until max_outputs is reached, then
+ * PGC_ENOMEM).  Asynchronous on the context's stream. */
+pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every);
+
+/* Copy the recorded time series to the host (synchronizes).  Any pointer may be NULL.
+ * h_t_fs[T]; h_mean[T][4], h_var[T][4] with columns (V_x m/s, V_y m/s, energy eV, J_x A/m);
+ * h_nodes[T][Q][4] per-node values.  *T_out = number of records (t = 0 included). */
+pgc_status pgc_moments(pgc_ctx *ctx, double *h_t_fs, double *h_mean, double *h_var,
+                       double *h_nodes, int64_t *T_out);
+
+/* Distribution of Eq. (24) reconstructed at nz arbitrary points h_z[nz][d] in [-1,1]^d
+ * (d = number of random inputs): counts h_hist[nz][Nk][Nk] and their maxima h_max[nz].
+ * Counts are non-negative; counts plus particles outside the grid equal N. */
+pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32_t *h_hist,
+                             uint32_t *h_max);
+
+/* State as FP64 on the host, layout [2][P][N] (synchronizes), and the reverse upload (the
+ * histogram of the uploaded state becomes f^n for the next step). */
+pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat);
+pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat);
+
+/* Counters PGC_CNT_* (uint64 [PGC_NUM_COUNTERS]); synchronizes. */
+pgc_status pgc_counters(pgc_ctx *ctx, uint64_t *h_counters);
+
+/* Current histogram f^n: h_hist[Q][Nk][Nk] and the normaliser Nmax[Q] of the Pauli test. */
+pgc_status pgc_get_hist(pgc_ctx *ctx, uint32_t *h_hist, uint32_t *h_nmax);
+
+/* Release the context (does not free the caller's buffers). NULL is a no-op. */
+void pgc_destroy(pgc_ctx *ctx);
+
+/* Message of the last failing call on ctx; ctx == NULL gives the last failure of a call that
+ * had no context (pgc_query_sizes, pgc_init). */
+const char *pgc_last_error(const pgc_ctx *ctx);
+const char *pgc_status_string(pgc_status s);
+
+/* Number of kernel launches issued by the library since load (for launch accounting). */
+uint64_t pgc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGC_H */

@@ -1,0 +1,731 @@
+// pgc_api.cu -- the C ABI of include/pgc.h: configuration checks, the FP64 host tables
+// (physical constants of Table 1 / Appendix A, Gauss-Legendre quadrature, Legendre basis,
+// densities), the device buffer carving, and the per-step launch sequence.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pgc.h"
+#include "pgc_device.cuh"
+#include "pgc_kernels.cuh"
+#include "pgc_runner.h"
+
+namespace pgc {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches += n; }
+
+Runner *make_runner(int P, int Q, int precision, const HostTables &t, const DevBuffers &b, int num_sms)
+{
+    if (P == 1 && Q == 1) return make_runner_1x1(precision, t, b, num_sms);
+    if (P == 6 && Q == 6) return make_runner_6x6(precision, t, b, num_sms);
+    if (P == 21 && Q == 36) return make_runner_21x36(precision, t, b, num_sms);
+    return nullptr;
+}
+
+// ------------------------------------------------------------------------------------------
+// Gauss-Legendre rule for the uniform density on [-1,1] by the Golub-Welsch method: the nodes
+// are the eigenvalues of the symmetric Jacobi matrix of the orthonormal Legendre recurrence,
+// the weights the squared first components of its normalised eigenvectors (total mass 1).
+// The eigenproblem is solved with cyclic Jacobi rotations.
+// ------------------------------------------------------------------------------------------
+static void golub_welsch(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    std::vector<double> A(n * n, 0.0), V(n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int k = 1; k < n; ++k) {
+        const double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[(k - 1) * n + k] = A[k * n + k - 1] = b;
+    }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+        if (off < 1e-34) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A J  (columns p, q)
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- J^T A  (rows p, q)
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // V <- V J
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[a * n + a] < A[b * n + b]; });
+    x.resize(n);
+    w.resize(n);
+    for (int j = 0; j < n; ++j) {
+        const int e = idx[j];
+        x[j] = A[e * n + e];
+        w[j] = V[0 * n + e] * V[0 * n + e];
+    }
+    // symmetric rule: enforce exact symmetry of nodes and weights
+    for (int j = 0; j < n / 2; ++j) {
+        const double xm = 0.5 * (x[n - 1 - j] - x[j]), wm = 0.5 * (w[j] + w[n - 1 - j]);
+        x[j] = -xm; x[n - 1 - j] = xm;
+        w[j] = wm; w[n - 1 - j] = wm;
+    }
+    if (n % 2) x[n / 2] = 0.0;
+}
+
+// orthonormal Legendre values psi_0..psi_M at z from the orthonormal three-term recurrence
+// z psi_n = b_{n+1} psi_{n+1} + b_n psi_{n-1},  b_n = n / sqrt(4 n^2 - 1)
+static void onb_legendre(int M, double z, double *out)
+{
+    out[0] = 1.0;
+    if (M == 0) return;
+    out[1] = z / (1.0 / std::sqrt(3.0));
+    for (int n = 1; n < M; ++n) {
+        const double bn = n / std::sqrt(4.0 * n * n - 1.0);
+        const double bn1 = (n + 1) / std::sqrt(4.0 * (n + 1) * (n + 1) - 1.0);
+        out[n + 1] = (z * out[n] - bn * out[n - 1]) / bn1;
+    }
+}
+
+// basis at a point z (d components), 2-D total degree in graded order (t - j, j)
+static void basis_at(int d, int M, const double *z, double *psi)
+{
+    if (d == 0) { psi[0] = 1.0; return; }
+    if (d == 1) { onb_legendre(M, z[0], psi); return; }
+    std::vector<double> a(M + 1), b(M + 1);
+    onb_legendre(M, z[0], a.data());
+    onb_legendre(M, z[1], b.data());
+    int h = 0;
+    for (int t = 0; t <= M; ++t)
+        for (int j = 0; j <= t; ++j) psi[h++] = a[t - j] * b[j];
+}
+
+static int dims_of(const pgc_config &c, int *P, int *Q)
+{
+    const bool er = c.eps0_eV.lo != c.eps0_eV.hi, fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
+    const int d = (int)er + (int)fr;
+    if (d == 0) { *P = 1; *Q = 1; }
+    else if (d == 1) { *P = c.degree_M + 1; *Q = c.quad_per_dim; }
+    else { *P = (c.degree_M + 1) * (c.degree_M + 2) / 2; *Q = c.quad_per_dim * c.quad_per_dim; }
+    return d;
+}
+
+// Physical constants of Table 1 (Sec. 5) and the closed-form rate prefactors of Appendix A.
+static void build_tables(const pgc_config &c, HostTables &t)
+{
+    const double e = 1.602176634e-19, hbar_eVs = 6.582119569e-16, kB = 8.617333262e-5;
+    const double hbar = hbar_eVs * e;            // J s
+    const double vF = 1.0e6;                     // 1e8 cm/s
+    const double sigma = 7.6e-8 * 10.0;          // 7.6e-8 g/cm^2 -> kg/m^2
+    const double vp = 2.0e4;                     // 2e6 cm/s
+    const double Dac = 6.8 * e;                  // J
+    const double DO = 1.0e9 * e * 100.0;         // eV/cm -> J/m
+    const double DK = 3.5e8 * e * 100.0;
+    const double hwO = 0.1646, hwK = 0.124;      // eV
+    const double Ni = 1.0e4 * 100.0;             // 1/m
+    const double V0 = 4.56e-14 * e * 1.0e-4;     // J m^2
+    const double a = 1.0e-8 * 1.0e-2;            // m
+    const double kT = kB * c.T_K;                // eV
+    const double kTJ = kT * e;
+    t.hbar_fs = hbar_eVs * 1.0e15;
+    t.hvF = hbar_eVs * vF * 1.0e9;               // eV nm
+    t.kT = kT;
+    t.hwO = hwO;
+    t.hwK = hwK;
+    t.nO = 1.0 / std::expm1(hwO / kT);
+    t.nK = 1.0 / std::expm1(hwK / kT);
+    const double hvFJ = hbar * vF;
+    // Gamma_ac / eps  [1/s per J] -> [1/fs per eV]
+    t.Cac = Dac * Dac * kTJ / (4.0 * hbar * hbar * hbar * vF * vF * sigma * vp * vp) * e * 1e-15;
+    t.CO = DO * DO / (hbar * hbar * vF * vF * sigma * (hwO / hbar_eVs)) * e * 1e-15;
+    t.CK = DK * DK / (hbar * hbar * vF * vF * sigma * (hwK / hbar_eVs)) * e * 1e-15;
+    // Gamma_edg = Ni V0^2 /(2 pi hbar W (hbar vF)^2) eps T, 1/W = eps0/(pi hbar vF)
+    t.Cedg = Ni * V0 * V0 / (2.0 * kPi * kPi * hbar * hvFJ * hvFJ * hvFJ) * e * e * 1e-15;
+    t.a_nm = a * 1e9;
+    t.Lk = c.Lk_hvF_eV / t.hvF;
+    t.dk = 2.0 * t.Lk / c.Nk;
+    t.vF_ms = vF;
+    t.mu = c.eps_F_eV;
+    t.alpha = c.alpha;
+    t.dt = c.dt_fs;
+    t.mech = c.mech_mask;
+    t.n_theta = c.n_theta_edge;
+    t.pauli_mode = c.pauli_norm;
+    t.final_state = c.final_state;
+    t.max_coll = c.max_collisions;
+    t.Nk = c.Nk;
+
+    int P, Q;
+    const int d = dims_of(c, &P, &Q);
+    t.d = d; t.P = P; t.Q = Q;
+    std::vector<double> x1, w1;
+    t.z.assign((size_t)Q * std::max(d, 1), 0.0);
+    t.w.assign(Q, 0.0);
+    if (d == 0) t.w[0] = 1.0;
+    else {
+        golub_welsch(c.quad_per_dim, x1, w1);
+        if (d == 1) for (int q = 0; q < Q; ++q) { t.z[q] = x1[q]; t.w[q] = w1[q]; }
+        else
+            for (int q1 = 0; q1 < c.quad_per_dim; ++q1)
+                for (int q2 = 0; q2 < c.quad_per_dim; ++q2) {
+                    const int q = q1 * c.quad_per_dim + q2;
+                    t.z[2 * q] = x1[q1]; t.z[2 * q + 1] = x1[q2];
+                    t.w[q] = w1[q1] * w1[q2];
+                }
+    }
+    const bool er = c.eps0_eV.lo != c.eps0_eV.hi, fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
+    t.psi.assign((size_t)Q * P, 0.0);
+    t.wpsi.assign((size_t)Q * P, 0.0);
+    t.eps0.assign(Q, 0.0); t.Ex.assign(Q, 0.0); t.dq.assign(Q, 0.0); t.nq.assign(Q, 0.0);
+    t.eps0_max = 0.0;
+    for (int q = 0; q < Q; ++q) {
+        double ze = 0.0, zf = 0.0;
+        if (d == 1) { if (er) ze = t.z[q]; else zf = t.z[q]; }
+        if (d == 2) { ze = t.z[2 * q]; zf = t.z[2 * q + 1]; }
+        t.eps0[q] = er ? c.eps0_eV.lo + 0.5 * (c.eps0_eV.hi - c.eps0_eV.lo) * (ze + 1.0) : c.eps0_eV.lo;
+        t.Ex[q] = fr ? c.Ex_Vcm.lo + 0.5 * (c.Ex_Vcm.hi - c.Ex_Vcm.lo) * (zf + 1.0) : c.Ex_Vcm.lo;
+        t.dq[q] = t.Ex[q] * 1.0e-7 * c.dt_fs / t.hbar_fs;
+        t.nq[q] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper(t.eps0[q], c.eps_F_eV, kT) * 1.0e18;
+        t.eps0_max = std::max(t.eps0_max, t.eps0[q]);
+        basis_at(d, c.degree_M, d ? &t.z[(size_t)q * d] : nullptr, &t.psi[(size_t)q * P]);
+        for (int h = 0; h < P; ++h) t.wpsi[(size_t)q * P + h] = t.w[q] * t.psi[(size_t)q * P + h];
+    }
+    t.dhat.assign(P, 0.0);
+    t.drift_mask = 0;
+    double dmax = 0.0;
+    for (int h = 0; h < P; ++h) {
+        double s = 0.0;
+        for (int q = 0; q < Q; ++q) s += t.wpsi[(size_t)q * P + h] * t.dq[q];
+        t.dhat[h] = s;
+        dmax = std::max(dmax, std::fabs(s));
+    }
+    // the field is affine in z: only the constant and the linear field mode are non-zero;
+    // quadrature round-off in the other entries is dropped
+    for (int h = 0; h < P; ++h) {
+        if (std::fabs(t.dhat[h]) <= 1e-13 * dmax) t.dhat[h] = 0.0;
+        if (t.dhat[h] != 0.0) t.drift_mask |= (1u << h);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// small kernels shared by all shapes
+// ------------------------------------------------------------------------------------------
+struct FinArgs {
+    double nq[64], w[64];
+    double N, vF_ms, t_fs;
+    int Q, g1, g2;
+};
+
+// fixed-order reduction of the block partials, node values, mean and variance (Sec. 4.2);
+// record = [t, nodes[Q][4] (Vx, Vy, E, Jx), mean[4], var[4]]
+__global__ void k_finalize(const double *part1, const double *part2, const __grid_constant__ FinArgs f, double *rec)
+{
+    __shared__ double S[64 * 3];
+    const int n3 = f.Q * 3;
+    for (int j = threadIdx.x; j < n3; j += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < f.g1; ++b) s += part1[(int64_t)b * n3 + j];
+        for (int b = 0; b < f.g2; ++b) s += part2[(int64_t)b * n3 + j];
+        S[j] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double qe = 1.602176634e-19;
+        rec[0] = f.t_fs;
+        double m[4] = {0, 0, 0, 0}, m2[4] = {0, 0, 0, 0};
+        for (int q = 0; q < f.Q; ++q) {
+            const double vx = S[q * 3 + 0] / f.N * f.vF_ms, vy = S[q * 3 + 1] / f.N * f.vF_ms;
+            const double en = S[q * 3 + 2] / f.N, jx = -qe * f.nq[q] * vx;
+            const double v[4] = {vx, vy, en, jx};
+            for (int o = 0; o < 4; ++o) {
+                rec[1 + q * 4 + o] = v[o];
+                m[o] += f.w[q] * v[o];
+                m2[o] += f.w[q] * v[o] * v[o];
+            }
+        }
+        for (int o = 0; o < 4; ++o) {
+            rec[1 + f.Q * 4 + o] = m[o];
+            rec[1 + f.Q * 4 + 4 + o] = m2[o] - m[o] * m[o];
+        }
+    }
+}
+
+// maximum over the cells of each node's histogram
+__global__ void k_hist_max(const uint32_t *H, int64_t cells, uint32_t *out)
+{
+    __shared__ uint32_t sm[32];
+    const uint32_t *h = H + (int64_t)blockIdx.x * cells;
+    uint32_t m = 0;
+    for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) m = max(m, h[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (blockDim.x >> 5)) ? sm[threadIdx.x] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) out[blockIdx.x] = m;
+    }
+}
+
+}  // namespace pgc
+
+using namespace pgc;
+
+struct pgc_ctx {
+    pgc_config cfg{};
+    HostTables t;
+    DevBuffers b;
+    Runner *run = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t step = 0;
+    int64_t T_out = 0;
+    int rec_len = 0;
+    double *series = nullptr;
+    uint32_t *tmp_max = nullptr;
+    bool failed = false;
+    std::string err;
+};
+
+static std::mutex g_err_mu;
+static std::string g_err;
+
+static pgc_status fail(pgc_ctx *ctx, pgc_status s, const std::string &msg)
+{
+    if (ctx) {
+        ctx->err = msg;
+        if (s == PGC_ECUDA) ctx->failed = true;
+    } else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_err = msg;
+    }
+    return s;
+}
+
+static pgc_status cuda_fail(pgc_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, PGC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+namespace {
+struct Layout {
+    int P = 1, Q = 1, d = 0;
+    int64_t ld = 0, hist_stride = 0;
+    size_t state = 0, hist = 0, scratch = 0;
+    size_t off_queue = 0, off_qcount = 0, off_counters = 0, off_nmax = 0, off_part1 = 0, off_part2 = 0,
+           off_series = 0, off_recon = 0, off_tmpmax = 0;
+    int rec_len = 0;
+};
+}  // namespace
+
+static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
+{
+    if (!c) { *msg = "cfg is NULL"; return PGC_EINVAL; }
+    auto bad = [&](const char *m) { *msg = m; return PGC_EINVAL; };
+    if (!(c->T_K > 0.0)) return bad("T_K must be > 0");
+    if (!(c->eps0_eV.lo > 0.0) || !(c->eps0_eV.hi >= c->eps0_eV.lo)) return bad("eps0 interval must satisfy 0 < lo <= hi");
+    if (!(c->Ex_Vcm.hi >= c->Ex_Vcm.lo) || !std::isfinite(c->Ex_Vcm.lo) || !std::isfinite(c->Ex_Vcm.hi))
+        return bad("Ex interval must satisfy lo <= hi (finite)");
+    if (c->mech_mask > 63u) return bad("mech_mask has unknown bits");
+    if (!(c->alpha >= 0.0) || !(c->alpha < 10.0)) return bad("alpha must be in [0, 10)");
+    if (c->Nk < 2 || c->Nk > 4096) return bad("Nk must be in [2, 4096]");
+    if (!(c->Lk_hvF_eV > 0.0)) return bad("Lk_hvF_eV must be > 0");
+    if (c->degree_M < 0 || c->degree_M > 30) return bad("degree_M must be in [0, 30]");
+    if (c->quad_per_dim < 1 || c->quad_per_dim > 32) return bad("quad_per_dim must be in [1, 32]");
+    if (c->n_particles < 1 || c->n_particles > 2000000000LL) return bad("n_particles must be in [1, 2e9]");
+    if (!(c->dt_fs > 0.0)) return bad("dt_fs must be > 0");
+    if (c->precision != PGC_FP32 && c->precision != PGC_FP64) return bad("precision must be PGC_FP32 or PGC_FP64");
+    if (c->pauli_norm < 0 || c->pauli_norm > 2) return bad("pauli_norm must be 0, 1 or 2");
+    if (c->final_state < 0 || c->final_state > 1) return bad("final_state must be 0 or 1");
+    if (c->n_theta_edge < 4 || c->n_theta_edge > kMaxTheta || (c->n_theta_edge & 1)) return bad("n_theta_edge must be even in [4, 256]");
+    if (c->max_collisions < 1 || c->max_collisions > 65535) return bad("max_collisions must be in [1, 65535]");
+    if (c->max_outputs < 1) return bad("max_outputs must be >= 1");
+    L->d = dims_of(*c, &L->P, &L->Q);
+    if (L->d > 0 && c->quad_per_dim < c->degree_M + 1) return bad("quad_per_dim must be >= degree_M + 1 (exact projection)");
+    const bool shape_ok = (L->P == 1 && L->Q == 1) || (L->P == 6 && L->Q == 6) || (L->P == 21 && L->Q == 36);
+    if (!shape_ok) {
+        *msg = "compiled (P,Q) shapes are (1,1), (6,6), (21,36); got (" + std::to_string(L->P) + "," + std::to_string(L->Q) + ")";
+        return PGC_EUNSUPPORTED;
+    }
+    const int64_t N = c->n_particles;
+    const size_t R = (c->precision == PGC_FP64) ? 8 : 4;
+    L->ld = round_up(N, 64);
+    L->state = (size_t)2 * L->P * L->ld * R;
+    L->hist_stride = round_up((int64_t)L->Q * c->Nk * c->Nk, 64);
+    L->hist = (size_t)3 * L->hist_stride * 4;
+    L->rec_len = 1 + 4 * L->Q + 8;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
+    L->off_queue = take((size_t)N * 4);
+    L->off_qcount = take(4 * 4);
+    L->off_counters = take(8 * 8);
+    L->off_nmax = take((size_t)L->Q * 4);
+    L->off_part1 = take((size_t)kMaxGrid1 * L->Q * 3 * 8);
+    L->off_part2 = take((size_t)kGrid2 * L->Q * 3 * 8);
+    L->off_series = take((size_t)c->max_outputs * L->rec_len * 8);
+    L->off_recon = take((size_t)c->Nk * c->Nk * 4);
+    L->off_tmpmax = take(4);
+    L->scratch = off;
+    return PGC_OK;
+}
+
+extern "C" {
+
+void pgc_config_default(pgc_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->T_K = 300.0;
+    c->eps_F_eV = 0.4;
+    c->eps0_eV.lo = c->eps0_eV.hi = 0.1;
+    c->Ex_Vcm.lo = c->Ex_Vcm.hi = 5000.0;
+    c->mech_mask = PGC_MECH_ALL;
+    c->alpha = 0.1;
+    c->Nk = 240;
+    c->Lk_hvF_eV = 5.0;
+    c->degree_M = 5;
+    c->quad_per_dim = 6;
+    c->n_particles = 10000;
+    c->dt_fs = 1.0;
+    c->seed = 1;
+    c->stream_id = 0;
+    c->precision = PGC_FP32;
+    c->pauli_norm = PGC_PAULI_INITIAL_MAX;
+    c->final_state = PGC_FS_PAPER;
+    c->n_theta_edge = 64;
+    c->max_collisions = 32;
+    c->max_outputs = 1024;
+}
+
+pgc_status pgc_query_sizes(const pgc_config *cfg, size_t *state_bytes, size_t *hist_bytes,
+                           size_t *scratch_bytes, int32_t *P, int32_t *Q)
+{
+    Layout L;
+    std::string msg;
+    pgc_status s = check_config(cfg, &L, &msg);
+    if (s != PGC_OK) return fail(nullptr, s, msg);
+    if (state_bytes) *state_bytes = L.state;
+    if (hist_bytes) *hist_bytes = L.hist;
+    if (scratch_bytes) *scratch_bytes = L.scratch;
+    if (P) *P = L.P;
+    if (Q) *Q = L.Q;
+    return PGC_OK;
+}
+
+static pgc_status observe_current(pgc_ctx *ctx, bool record, bool set_nmax)
+{
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    const int cur = (int)(ctx->step % 3);
+    if ((e = cudaMemsetAsync(ctx->b.hist, 0, (size_t)3 * ctx->b.hist_stride * 4, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "memset hist");
+    if ((e = ctx->run->observe(cur, s)) != cudaSuccess) return cuda_fail(ctx, e, "observe");
+    const int64_t cells = (int64_t)ctx->t.Nk * ctx->t.Nk;
+    if (set_nmax) {
+        k_hist_max<<<ctx->t.Q, 256, 0, s>>>(ctx->b.hist + (int64_t)cur * ctx->b.hist_stride, cells, ctx->b.nmax);
+        count_launch();
+    }
+    if (record) {
+        if (ctx->T_out >= ctx->cfg.max_outputs) return fail(ctx, PGC_ENOMEM, "moment series full (max_outputs)");
+        FinArgs f{};
+        for (int q = 0; q < ctx->t.Q; ++q) { f.nq[q] = ctx->t.nq[q]; f.w[q] = ctx->t.w[q]; }
+        f.N = (double)ctx->b.N;
+        f.vF_ms = ctx->t.vF_ms;
+        f.t_fs = ctx->step * ctx->t.dt;
+        f.Q = ctx->t.Q;
+        f.g1 = ctx->run->grid1();
+        f.g2 = 0;
+        k_finalize<<<1, 128, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
+        count_launch();
+        ctx->T_out++;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "observe launch");
+    return PGC_OK;
+}
+
+pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_scratch,
+                    const double *h_init_khat, void *stream, pgc_ctx **out)
+{
+    if (!out) return fail(nullptr, PGC_EINVAL, "out is NULL");
+    *out = nullptr;
+    Layout L;
+    std::string msg;
+    pgc_status st = check_config(cfg, &L, &msg);
+    if (st != PGC_OK) return fail(nullptr, st, msg);
+    if (!d_state || !d_hist || !d_scratch) return fail(nullptr, PGC_EINVAL, "device buffers must be non-NULL");
+    if (((uintptr_t)d_state & 255) || ((uintptr_t)d_hist & 255) || ((uintptr_t)d_scratch & 255))
+        return fail(nullptr, PGC_EINVAL, "device buffers must be 256-byte aligned");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, PGC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, PGC_ECUDA, std::string("attribute: ") + cudaGetErrorString(e));
+
+    pgc_ctx *ctx = new (std::nothrow) pgc_ctx();
+    if (!ctx) return fail(nullptr, PGC_ENOMEM, "context allocation");
+    ctx->cfg = *cfg;
+    ctx->stream = (cudaStream_t)stream;
+    build_tables(*cfg, ctx->t);
+    char *scr = (char *)d_scratch;
+    DevBuffers &b = ctx->b;
+    b.state = d_state;
+    b.N = cfg->n_particles;
+    b.ld = L.ld;
+    b.hist = (uint32_t *)d_hist;
+    b.hist_stride = L.hist_stride;
+    b.queue = (uint32_t *)(scr + L.off_queue);
+    b.qcount = (uint32_t *)(scr + L.off_qcount);
+    b.counters = (unsigned long long *)(scr + L.off_counters);
+    b.nmax = (uint32_t *)(scr + L.off_nmax);
+    b.part1 = (double *)(scr + L.off_part1);
+    b.part2 = (double *)(scr + L.off_part2);
+    b.recon_hist = (uint32_t *)(scr + L.off_recon);
+    b.key0 = (uint32_t)cfg->seed;
+    b.key1 = (uint32_t)(cfg->seed >> 32);
+    b.stream_id = cfg->stream_id;
+    ctx->series = (double *)(scr + L.off_series);
+    ctx->tmp_max = (uint32_t *)(scr + L.off_tmpmax);
+    ctx->rec_len = L.rec_len;
+    ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
+    if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
+
+    cudaStream_t s = ctx->stream;
+    if ((e = cudaMemsetAsync(d_scratch, 0, L.scratch, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_state, 0, L.state, s)) != cudaSuccess) {
+        delete ctx->run; delete ctx;
+        return fail(nullptr, PGC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
+    }
+    if (h_init_khat) {
+        st = pgc_set_state(ctx, h_init_khat);
+        if (st == PGC_OK) st = observe_current(ctx, true, true);
+    } else {
+        if ((e = ctx->run->init_sample(s)) != cudaSuccess) st = cuda_fail(ctx, e, "init kernel");
+        else st = observe_current(ctx, true, true);
+    }
+    if (st != PGC_OK) {
+        std::string m = ctx->err;
+        delete ctx->run; delete ctx;
+        return fail(nullptr, st, m);
+    }
+    *out = ctx;
+    return PGC_OK;
+}
+
+pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    if (n_steps < 0) return fail(ctx, PGC_EINVAL, "n_steps < 0");
+    int64_t outs = 0;
+    if (moments_every > 0) outs = (ctx->step + n_steps) / moments_every - ctx->step / moments_every;
+    if (ctx->T_out + outs > ctx->cfg.max_outputs) return fail(ctx, PGC_ENOMEM, "moment series would exceed max_outputs");
+    cudaStream_t s = ctx->stream;
+    const int64_t cells = (int64_t)ctx->t.Nk * ctx->t.Nk;
+    FinArgs f{};
+    for (int q = 0; q < ctx->t.Q; ++q) { f.nq[q] = ctx->t.nq[q]; f.w[q] = ctx->t.w[q]; }
+    f.N = (double)ctx->b.N;
+    f.vF_ms = ctx->t.vF_ms;
+    f.Q = ctx->t.Q;
+    f.g1 = ctx->run->grid1();
+    f.g2 = kGrid2;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int64_t n = ctx->step;
+        const bool out = moments_every > 0 && ((n + 1) % moments_every == 0);
+        if (ctx->t.pauli_mode == PGC_PAULI_CURRENT_MAX) {
+            k_hist_max<<<ctx->t.Q, 256, 0, s>>>(ctx->b.hist + (int64_t)(n % 3) * ctx->b.hist_stride, cells, ctx->b.nmax);
+            count_launch();
+        }
+        cudaError_t e = ctx->run->step(n, out, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->step = n + 1;
+        if (out) {
+            f.t_fs = ctx->step * ctx->t.dt;
+            k_finalize<<<1, 128, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
+            count_launch();
+            ctx->T_out++;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
+    return PGC_OK;
+}
+
+pgc_status pgc_moments(pgc_ctx *ctx, double *h_t_fs, double *h_mean, double *h_var, double *h_nodes, int64_t *T_out)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const int64_t T = ctx->T_out;
+    const int Q = ctx->t.Q, RL = ctx->rec_len;
+    std::vector<double> buf((size_t)T * RL);
+    cudaError_t e = cudaSuccess;
+    if (T > 0) e = cudaMemcpyAsync(buf.data(), ctx->series, buf.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "moments copy");
+    for (int64_t t = 0; t < T; ++t) {
+        const double *r = &buf[(size_t)t * RL];
+        if (h_t_fs) h_t_fs[t] = r[0];
+        if (h_nodes) std::memcpy(h_nodes + (size_t)t * Q * 4, r + 1, sizeof(double) * Q * 4);
+        if (h_mean) std::memcpy(h_mean + (size_t)t * 4, r + 1 + Q * 4, sizeof(double) * 4);
+        if (h_var) std::memcpy(h_var + (size_t)t * 4, r + 1 + Q * 4 + 4, sizeof(double) * 4);
+    }
+    if (T_out) *T_out = T;
+    return PGC_OK;
+}
+
+pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat)
+{
+    if (!ctx || !h_khat) return fail(ctx, PGC_EINVAL, "NULL argument");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const int P = ctx->t.P;
+    const int64_t N = ctx->b.N, ld = ctx->b.ld;
+    const bool f64 = ctx->cfg.precision == PGC_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    std::vector<char> tmp((size_t)2 * P * ld * esz);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), ctx->b.state, tmp.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
+    for (int p = 0; p < 2 * P; ++p)
+        for (int64_t i = 0; i < N; ++i)
+            h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp.data())[(size_t)p * ld + i]
+                                            : (double)((const float *)tmp.data())[(size_t)p * ld + i];
+    return PGC_OK;
+}
+
+pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
+{
+    if (!ctx || !h_khat) return fail(ctx, PGC_EINVAL, "NULL argument");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const int P = ctx->t.P;
+    const int64_t N = ctx->b.N, ld = ctx->b.ld;
+    const bool f64 = ctx->cfg.precision == PGC_FP64;
+    const size_t esz = f64 ? 8 : 4;
+    std::vector<char> tmp((size_t)2 * P * ld * esz, 0);
+    for (int p = 0; p < 2 * P; ++p)
+        for (int64_t i = 0; i < N; ++i) {
+            const double v = h_khat[(size_t)p * N + i];
+            if (f64) ((double *)tmp.data())[(size_t)p * ld + i] = v;
+            else ((float *)tmp.data())[(size_t)p * ld + i] = (float)v;
+        }
+    cudaError_t e = cudaMemcpyAsync(ctx->b.state, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
+    // the histogram of the uploaded state becomes f^n (the Pauli normaliser is kept)
+    if (ctx->T_out > 0) return observe_current(ctx, false, false);
+    return PGC_OK;
+}
+
+pgc_status pgc_counters(pgc_ctx *ctx, uint64_t *h)
+{
+    if (!ctx || !h) return fail(ctx, PGC_EINVAL, "NULL argument");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    unsigned long long c[8];
+    cudaError_t e = cudaMemcpyAsync(c, ctx->b.counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "counters copy");
+    for (int k = 0; k < 8; ++k) h[k] = c[k];
+    h[PGC_CNT_STEPS] = (uint64_t)ctx->step;
+    return PGC_OK;
+}
+
+pgc_status pgc_get_hist(pgc_ctx *ctx, uint32_t *h_hist, uint32_t *h_nmax)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const int cur = (int)(ctx->step % 3);
+    cudaError_t e = cudaSuccess;
+    if (h_hist)
+        e = cudaMemcpyAsync(h_hist, ctx->b.hist + (int64_t)cur * ctx->b.hist_stride,
+                            (size_t)ctx->t.Q * ctx->t.Nk * ctx->t.Nk * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && h_nmax)
+        e = cudaMemcpyAsync(h_nmax, ctx->b.nmax, (size_t)ctx->t.Q * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hist copy");
+    return PGC_OK;
+}
+
+pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32_t *h_hist, uint32_t *h_max)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    if (nz < 0 || (nz > 0 && ((!h_z && ctx->t.d > 0) || !h_hist || !h_max))) return fail(ctx, PGC_EINVAL, "bad arguments");
+    const int d = ctx->t.d, P = ctx->t.P;
+    const int64_t cells = (int64_t)ctx->t.Nk * ctx->t.Nk;
+    std::vector<double> psi(P);
+    for (int j = 0; j < nz; ++j) {
+        if (d > 0)
+            for (int k = 0; k < d; ++k)
+                if (!(h_z[(size_t)j * d + k] >= -1.0 && h_z[(size_t)j * d + k] <= 1.0))
+                    return fail(ctx, PGC_EINVAL, "z outside [-1,1]");
+        basis_at(d, ctx->cfg.degree_M, d ? &h_z[(size_t)j * d] : nullptr, psi.data());
+        cudaError_t e = cudaMemsetAsync(ctx->b.recon_hist, 0, cells * 4, ctx->stream);
+        if (e == cudaSuccess) e = ctx->run->hist_at(psi.data(), ctx->b.recon_hist, ctx->stream);
+        if (e == cudaSuccess) {
+            k_hist_max<<<1, 256, 0, ctx->stream>>>(ctx->b.recon_hist, cells, ctx->tmp_max);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_hist + (size_t)j * cells, ctx->b.recon_hist, cells * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_max + j, ctx->tmp_max, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct_f");
+    }
+    return PGC_OK;
+}
+
+void pgc_destroy(pgc_ctx *ctx)
+{
+    if (!ctx) return;
+    delete ctx->run;
+    delete ctx;
+}
+
+const char *pgc_last_error(const pgc_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    static thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    copy = g_err;
+    return copy.c_str();
+}
+
+const char *pgc_status_string(pgc_status s)
+{
+    switch (s) {
+    case PGC_OK: return "PGC_OK";
+    case PGC_EINVAL: return "PGC_EINVAL";
+    case PGC_ENOMEM: return "PGC_ENOMEM";
+    case PGC_ECUDA: return "PGC_ECUDA";
+    case PGC_ESTATE: return "PGC_ESTATE";
+    case PGC_ETIMEOUT: return "PGC_ETIMEOUT";
+    case PGC_EUNSUPPORTED: return "PGC_EUNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+uint64_t pgc_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

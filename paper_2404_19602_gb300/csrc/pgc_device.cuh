@@ -1,0 +1,349 @@
+// pgc_device.cuh -- device building blocks of the particle stochastic-Galerkin step
+// (arXiv:2404.19602): counter-based random numbers, the closed-form scattering rates of
+// Appendix A, the final-state maps h^1..h^7 of Sec. 3, the grid of the Pauli test, and the
+// Fermi-Dirac sampler of the initial state.  Everything is templated on the arithmetic type R
+// (float for the production path, double for the FP64 mode).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pgc {
+
+constexpr int kMaxTheta = 256;   // upper bound of the edge trapezoid points
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------------------------------
+// Physical constants of one context, prepared on the host in FP64 and stored in R.
+// Rates are in 1/fs; energies eV; wave-vectors nm^-1.
+// ------------------------------------------------------------------------------------------
+template <typename R>
+struct Phys {
+    R hvF, hvF2;          // hbar vF (eV nm) and its square
+    R Lk, dk, inv_dk;     // grid half-width, cell size, 1/cell size
+    R alpha1;             // 1 + alpha
+    R dt;                 // fs
+    R Cac;                // Gamma_ac = Cac * eps
+    R COm, COp, CKm, CKp; // Gamma_O- = COm (eps - hwO) H(..), Gamma_O+ = COp (eps + hwO) ...
+    R hwO, hwK;           // phonon energies, eV
+    R wOk, wKk;           // hbar omega / (hbar vF): |k| change of the paper's final states
+    R Cedg;               // Gamma_edg = Cedg * eps0 * eps * T(|k|, cos th)
+    R two_a2;             // 2 a^2 (nm^2)
+    R edge_h;             // 2 pi / n_theta
+    R bound_edge;         // 2 pi * (1 + 1e-5): upper bound of the trapezoid T
+    R vF_ms;              // vF in m/s
+    R cosj[kMaxTheta + 1];// cos(2 pi j / n_theta), j = 0..n_theta
+    uint32_t mech;
+    int32_t n_theta;
+    int32_t pauli_mode;   // 0 initial max, 1 current max, 2 off
+    int32_t final_state;  // 0 paper, 1 exact energy
+    int32_t max_coll;
+    int32_t Nk;
+};
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, two multipliers, Weyl keys.
+// ------------------------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// odd multiples of 2^-24 in (0,1): identical values in FP32 and FP64
+template <typename R> __device__ __forceinline__ R u01(uint32_t x)
+{
+    return (R)((x >> 8) | 1u) * (R)5.9604644775390625e-8;
+}
+
+template <typename R> __device__ __forceinline__ R rlog(R x);
+template <> __device__ __forceinline__ float rlog<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double rlog<double>(double x) { return log(x); }
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return sqrt(x); }
+template <typename R> __device__ __forceinline__ R rexp(R x);
+template <> __device__ __forceinline__ float rexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+template <typename R> __device__ __forceinline__ void rsincos(R x, R *s, R *c);
+template <> __device__ __forceinline__ void rsincos<float>(float x, float *s, float *c) { sincosf(x, s, c); }
+template <> __device__ __forceinline__ void rsincos<double>(double x, double *s, double *c) { sincos(x, s, c); }
+template <typename R> __device__ __forceinline__ R rsin(R x);
+template <> __device__ __forceinline__ float rsin<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double rsin<double>(double x) { return sin(x); }
+template <typename R> __device__ __forceinline__ R rfloor(R x);
+template <> __device__ __forceinline__ float rfloor<float>(float x) { return floorf(x); }
+template <> __device__ __forceinline__ double rfloor<double>(double x) { return floor(x); }
+
+// ------------------------------------------------------------------------------------------
+// Cell of a wave-vector on the fixed grid [-Lk, Lk]^2 (Sec. 3); -1 outside.  The FP64 mode
+// divides (as the definition reads); the FP32 mode multiplies by the reciprocal.
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int cell_of(const Phys<R> &ph, R kx, R ky)
+{
+    R fr, fl;
+    if constexpr (sizeof(R) == 8) {
+        fr = floor((kx + ph.Lk) / ph.dk);
+        fl = floor((ky + ph.Lk) / ph.dk);
+    } else {
+        fr = floorf((kx + ph.Lk) * ph.inv_dk);
+        fl = floorf((ky + ph.Lk) * ph.inv_dk);
+    }
+    const R nk = (R)ph.Nk;
+    if (!(fr >= (R)0) || !(fl >= (R)0) || fr >= nk || fl >= nk) return -1;
+    return (int)fr * ph.Nk + (int)fl;
+}
+
+// ------------------------------------------------------------------------------------------
+// Edge integral T(|k|, c) = int_0^{2pi} exp(-beta (cos th' - c)^2) d th' by the trapezoid rule
+// on n_theta points (Appendix A), using the mirror symmetry th' -> 2pi - th'.
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R edge_T(const Phys<R> &ph, R beta, R c)
+{
+    const int half = ph.n_theta >> 1;
+    R x0 = ph.cosj[0] - c, xh = ph.cosj[half] - c;
+    R s = rexp<R>(-beta * x0 * x0) + rexp<R>(-beta * xh * xh);
+    R inner = (R)0;
+    for (int j = 1; j < half; ++j) {
+        const R x = ph.cosj[j] - c;
+        inner += rexp<R>(-beta * x * x);
+    }
+    return ph.edge_h * (s + (R)2 * inner);
+}
+
+// Rates of the six mechanisms of Eq. (20) at one state (Appendix A closed forms).  Returns the sum.
+template <typename R>
+__device__ __forceinline__ R rates6(const Phys<R> &ph, R kx, R ky, R eps0, R g[6])
+{
+    const R kk = kx * kx + ky * ky;
+    const R eps = rsqrt_<R>(ph.hvF2 * kk + eps0 * eps0);
+    const uint32_t m = ph.mech;
+    g[0] = (m & 1u) ? ph.Cac * eps : (R)0;
+    g[1] = ((m & 2u) && (eps - ph.hwO - eps0 > (R)0)) ? ph.COm * (eps - ph.hwO) : (R)0;
+    g[2] = ((m & 4u) && (eps + ph.hwO - eps0 > (R)0)) ? ph.COp * (eps + ph.hwO) : (R)0;
+    g[3] = ((m & 8u) && (eps - ph.hwK - eps0 > (R)0)) ? ph.CKm * (eps - ph.hwK) : (R)0;
+    g[4] = ((m & 16u) && (eps + ph.hwK - eps0 > (R)0)) ? ph.CKp * (eps + ph.hwK) : (R)0;
+    if (m & 32u) {
+        const R km = rsqrt_<R>(kk);
+        const R c = (km > (R)0) ? kx / km : (R)1;
+        g[5] = ph.Cedg * eps0 * eps * edge_T<R>(ph, ph.two_a2 * kk, c);
+    } else {
+        g[5] = (R)0;
+    }
+    return ((g[0] + g[1]) + (g[2] + g[3])) + (g[4] + g[5]);
+}
+
+// Upper bound of sum_nu Gamma_nu over all states with energy <= eps and band minimum <= eps0max:
+// every closed form is non-decreasing in eps, the Heaviside factors are dropped, T <= 2pi.
+template <typename R>
+__device__ __forceinline__ R rate_bound(const Phys<R> &ph, R eps, R eps0max)
+{
+    const uint32_t m = ph.mech;
+    R s = (R)0;
+    if (m & 1u) s += ph.Cac * eps;
+    if (m & 2u) s += ph.COm * fmax(eps - ph.hwO, (R)0);
+    if (m & 4u) s += ph.COp * (eps + ph.hwO);
+    if (m & 8u) s += ph.CKm * fmax(eps - ph.hwK, (R)0);
+    if (m & 16u) s += ph.CKp * (eps + ph.hwK);
+    if (m & 32u) s += ph.Cedg * eps0max * eps * ph.bound_edge;
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// Angle laws of the final states (Sec. 3).  One uniform u per collision, shared by all nodes.
+// (1 + cos th) on [0, 2pi): solve th + sin th = 2 pi u ; (1 - cos th): th - sin th = 2 pi u.
+// Both maps are monotone; bisection to the working precision.
+// ------------------------------------------------------------------------------------------
+template <typename R>
+__device__ R solve_angle(R u, R sgn)
+{
+    const R t = (R)(2.0 * kPi) * u;
+    R lo = (R)0, hi = (R)(2.0 * kPi);
+    const int iters = (sizeof(R) == 8) ? 60 : 28;
+    for (int it = 0; it < iters; ++it) {
+        const R mid = (R)0.5 * (lo + hi);
+        if (mid + sgn * rsin<R>(mid) < t) lo = mid; else hi = mid;
+    }
+    return (R)0.5 * (lo + hi);
+}
+
+// Edge final angle: absolute angle with density exp(-beta (c - cos th')^2), inverted through
+// the trapezoid CDF on the n_theta grid, linear between grid points.
+template <typename R>
+__device__ R edge_angle(const Phys<R> &ph, R beta, R c, R u)
+{
+    const int n = ph.n_theta;
+    // total first (the grid values are cheap to recompute)
+    R prev = rexp<R>(-beta * (ph.cosj[0] - c) * (ph.cosj[0] - c));
+    R total = (R)0;
+    for (int j = 1; j <= n; ++j) {
+        const R x = ph.cosj[j] - c;
+        const R g = rexp<R>(-beta * x * x);
+        total += (R)0.5 * ph.edge_h * (prev + g);
+        prev = g;
+    }
+    const R target = u * total;
+    R C = (R)0;
+    prev = rexp<R>(-beta * (ph.cosj[0] - c) * (ph.cosj[0] - c));
+    for (int j = 1; j <= n; ++j) {
+        const R x = ph.cosj[j] - c;
+        const R g = rexp<R>(-beta * x * x);
+        const R Cn = C + (R)0.5 * ph.edge_h * (prev + g);
+        if (Cn > target || j == n) {
+            const R frac = (target - C) / (Cn - C);
+            return ((R)(j - 1) + frac) * ph.edge_h;
+        }
+        C = Cn;
+        prev = g;
+    }
+    return (R)0;
+}
+
+// Lazily computed angles of one collision event (common to every node)
+template <typename R>
+struct EventAngles {
+    R u;
+    R th_ac, th_k;
+    bool have_ac, have_k;
+    __device__ void reset(R uu) { u = uu; have_ac = have_k = false; }
+    __device__ R ac() { if (!have_ac) { th_ac = solve_angle<R>(u, (R)1); have_ac = true; } return th_ac; }
+    __device__ R kk() { if (!have_k) { th_k = solve_angle<R>(u, (R)-1); have_k = true; } return th_k; }
+};
+
+// Final state h^l(k) of mechanism l (0..5) at one node (Sec. 3).  Self scattering (l = 6) is
+// handled by the caller.
+template <typename R>
+__device__ __forceinline__ void final_state(const Phys<R> &ph, int l, R kx, R ky, R eps0,
+                                            EventAngles<R> &ang, R *nkx, R *nky)
+{
+    const R kk = kx * kx + ky * ky;
+    const R km = rsqrt_<R>(kk);
+    if (l == 5) {  // edge: absolute final angle, |k'| = |k|
+        const R c = (km > (R)0) ? kx / km : (R)1;
+        const R th = edge_angle<R>(ph, ph.two_a2 * kk, c, ang.u);
+        R s, co;
+        rsincos<R>(th, &s, &co);
+        *nkx = km * co;
+        *nky = km * s;
+        return;
+    }
+    const R ci = (km > (R)0) ? kx / km : (R)1;
+    const R si = (km > (R)0) ? ky / km : (R)0;
+    R th, kn;
+    if (l == 0) {
+        th = ang.ac();
+        kn = km;
+    } else {
+        const bool emit = (l == 1 || l == 3);
+        const bool opt = (l == 1 || l == 2);
+        th = opt ? (R)(2.0 * kPi) * ang.u : ang.kk();
+        const R hw = opt ? ph.hwO : ph.hwK;
+        if (ph.final_state == 1) {
+            const R eps = rsqrt_<R>(ph.hvF2 * kk + eps0 * eps0);
+            const R ep = emit ? eps - hw : eps + hw;
+            kn = rsqrt_<R>(ep * ep - eps0 * eps0) / ph.hvF;
+        } else {
+            const R dk = opt ? ph.wOk : ph.wKk;
+            kn = emit ? km - dk : km + dk;
+        }
+    }
+    R st, ct;
+    rsincos<R>(th, &st, &ct);
+    *nkx = kn * (ct * ci - st * si);
+    *nky = kn * (st * ci + ct * si);
+}
+
+// Pauli acceptance of a candidate in a cell: f = H / Nmax < eta with eta = m 2^-24 (m odd),
+// decided exactly in integers: H 2^24 < m Nmax.  Outside the grid or Nmax = 0: f = 0, accept.
+__device__ __forceinline__ bool pauli_accept(uint32_t H, uint32_t nmax, uint32_t eta_bits)
+{
+    if (nmax == 0u) return true;
+    const uint64_t m = (uint64_t)((eta_bits >> 8) | 1u);
+    return ((uint64_t)H << 24) < m * (uint64_t)nmax;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fermi-Dirac initial state (Sec. 2): energy density eps * FD(eps) on [eps0, inf).
+// int_e^inf x/(1+exp((x-mu)/kT)) dx = kT [ mu ln(1+e^-b) + kT (b ln(1+e^-b) - Li2(-e^-b)) ],
+// b = (e - mu)/kT.  Li2 for negative arguments: Bernoulli series in t = -ln(1 - x) on
+// [-1, 0], inversion formula below -1.
+// ------------------------------------------------------------------------------------------
+__host__ __device__ inline double li2_bern(double x)
+{
+    // x in [-1, 0]:  Li2(x) = sum_n B_n t^{n+1}/(n+1)!,  t = -ln(1 - x),  |t| <= ln 2
+    const double t = -log1p(-x);
+    const double B[12] = {1.0 / 6.0, -1.0 / 30.0, 1.0 / 42.0, -1.0 / 30.0, 5.0 / 66.0,
+                          -691.0 / 2730.0, 7.0 / 6.0, -3617.0 / 510.0, 43867.0 / 798.0,
+                          -174611.0 / 330.0, 854513.0 / 138.0, -236364091.0 / 2730.0};
+    double s = t - 0.25 * t * t;  // B_0 t + B_1 t^2 / 2
+    double t2 = t * t, p = t * t2, fact = 6.0;  // t^3 / 3!
+    for (int k = 0; k < 12; ++k) {
+        s += B[k] * p / fact;
+        const double n = 2.0 * k + 3.0;  // next odd power
+        p *= t2;
+        fact *= (n + 1.0) * (n + 2.0);
+    }
+    return s;
+}
+
+__host__ __device__ inline double li2_negative(double x)
+{
+    if (x >= -1.0) return li2_bern(x);
+    const double l = log(-x);
+    return -kPi * kPi / 6.0 - 0.5 * l * l - li2_bern(1.0 / x);
+}
+
+__host__ __device__ inline double fd_upper(double e, double mu, double kT)
+{
+    const double b = (e - mu) / kT;
+    const double l = (b > 0.0) ? log1p(exp(-b)) : -b + log1p(exp(b));
+    double li;
+    if (b > 700.0) li = 0.0;
+    else if (b < -700.0) li = -kPi * kPi / 6.0 - 0.5 * b * b;
+    else li = li2_negative(-exp(-b));
+    return kT * (mu * l + kT * (b * l - li));
+}
+
+// eps with F(eps) = u for the density eps*FD on [eps0, inf): bisection, then Newton polish
+__host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, double u)
+{
+    const double tot = fd_upper(eps0, mu, kT);
+    double lo = eps0, hi = fmax(mu, eps0) + 80.0 * kT;
+    auto resid = [&](double e) {  // F(e) - u  (upper-tail form for u >= 1/2)
+        return (u < 0.5) ? (tot - fd_upper(e, mu, kT)) / tot - u : (1.0 - u) - fd_upper(e, mu, kT) / tot;
+    };
+    for (int it = 0; it < 40; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (resid(mid) < 0.0) lo = mid; else hi = mid;
+    }
+    double e = 0.5 * (lo + hi);
+    for (int it = 0; it < 12; ++it) {
+        const double r = resid(e);
+        const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
+        if (!(dens > 0.0)) break;
+        double en = e - r / dens;
+        if (en <= lo || en >= hi) en = 0.5 * (lo + hi);
+        if (r < 0.0) lo = e; else hi = e;
+        if (fabs(en - e) <= 1e-16 * e) { e = en; break; }
+        e = en;
+    }
+    return e;
+}
+
+}  // namespace pgc

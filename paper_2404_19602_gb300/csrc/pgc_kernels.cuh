@@ -1,0 +1,456 @@
+// pgc_kernels.cuh -- the time-step kernels of the particle stochastic-Galerkin scheme
+// (arXiv:2404.19602, Algorithm 1 for P = Q = 1, Algorithm 2 otherwise), templated on the gPC
+// basis size P, the number of quadrature nodes Q and the arithmetic type R.
+//
+// One time step n is two launches on the context stream:
+//   k_phase1 (every particle, streaming): drift of the coefficients (Eq. (17), Sec. 4.1),
+//       reconstruction at the Q nodes (Eq. (23)), first flight-time draw, and a conservative
+//       rate bound that proves "no collision in this step" for most particles; those are
+//       finished here (histogram f^{n+1} of Eq. (24), moments).  The rest are appended to a
+//       collider queue.  It also clears the histogram buffer of step n+2 and the next queue
+//       counter, so that no separate memset is needed.
+//   k_phase2 (queued particles only): the exact collision loop of Algorithm 1 / 2 with the
+//       Pauli test against f^n, then the histogram f^{n+1} and moments of the final state.
+// On moment steps a one-block k_finalize reduces the block partial sums in a fixed order and
+// writes the node values, mean and variance of the record (Sec. 4.2).
+#pragma once
+
+#include "pgc_device.cuh"
+
+namespace pgc {
+
+constexpr int kPhase1Threads = 256;
+constexpr int kPhase2Threads = 128;
+constexpr int kMaxGrid1 = 4096;   // block partials sized for at most this many phase-1 blocks
+constexpr int kGrid2 = 608;       // phase-2 blocks (grid-stride over the queue)
+
+// Quadrature / basis tables of one context (Sec. 4.1).
+template <int P, int Q, typename R>
+struct Nodes {
+    R psi[Q * P];    // Psi_h(z_q), [q][h]
+    R wpsi[Q * P];   // w_q Psi_h(z_q)
+    R dhat[P];       // per-step drift of the x coefficients
+    R eps0[Q];       // band minimum at the node
+    R dq[Q];         // per-step drift (e/hbar) E(z_q) dt at the node
+    R eps0_max;
+    uint32_t drift_mask;  // coefficients h with dhat[h] != 0
+};
+
+template <int P, int Q, typename R>
+struct StepArgs {
+    Phys<R> ph;
+    Nodes<P, Q, R> nd;
+    R *khat;                 // [2][P][ld]
+    int64_t N, ld;
+    const uint32_t *Hcur;    // f^n   [Q][Nk*Nk]
+    uint32_t *Hnext;         // f^{n+1}
+    uint32_t *Hclear;        // buffer of step n+2, cleared by phase 1
+    int64_t hist_elems;      // Q*Nk*Nk
+    const uint32_t *nmax;    // [Q]
+    uint32_t *queue;         // [N]
+    uint32_t *qcount;        // collider count of this step
+    uint32_t *qcount_next;   // counter of the next step (zeroed by phase 1)
+    double *part1;           // [gridDim(phase1)][Q*3]
+    double *part2;           // [kGrid2][Q*3]
+    unsigned long long *counters;
+    uint32_t key0, key1, stream_id, step;
+    int32_t out_step;        // 1: accumulate the moments of the post-step state
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int P, int Q, typename R>
+__device__ __forceinline__ void load_coeffs(const StepArgs<P, Q, R> &a, int64_t i, R cx[P], R cy[P])
+{
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+        cx[h] = a.khat[(int64_t)h * a.ld + i];
+        cy[h] = a.khat[(int64_t)(P + h) * a.ld + i];
+    }
+}
+
+template <int P, int Q, typename R>
+__device__ __forceinline__ void recon_node(const Nodes<P, Q, R> &nd, int q, const R cx[P], const R cy[P],
+                                           R &kx, R &ky)
+{
+    R sx = (R)0, sy = (R)0;
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+        sx += cx[h] * nd.psi[q * P + h];
+        sy += cy[h] * nd.psi[q * P + h];
+    }
+    kx = sx;
+    ky = sy;
+}
+
+// group velocity (units of vF) and energy at one node (Sec. 2)
+template <typename R>
+__device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, float &vx, float &vy, float &e)
+{
+    const R eps = rsqrt_<R>(ph.hvF2 * (kx * kx + ky * ky) + eps0 * eps0);
+    vx = (float)(ph.hvF * kx / eps);
+    vy = (float)(ph.hvF * ky / eps);
+    e = (float)eps;
+}
+
+// ------------------------------------------------------------------------------------------
+// Phase 1: every particle.
+// ------------------------------------------------------------------------------------------
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(kPhase1Threads)
+k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
+{
+    constexpr int NW = kPhase1Threads / 32;
+    __shared__ double smom[NW][Q * 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // housekeeping for the next steps
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.qcount_next = 0u;
+    {
+        uint4 *hc = reinterpret_cast<uint4 *>(a.Hclear);
+        const int64_t n4 = a.hist_elems >> 2;
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n4;
+             j += (int64_t)gridDim.x * blockDim.x)
+            hc[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (blockIdx.x == 0)
+            for (int64_t j = (n4 << 2) + threadIdx.x; j < a.hist_elems; j += blockDim.x) a.Hclear[j] = 0u;
+    }
+    if (a.out_step)
+        for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
+
+    const Phys<R> &ph = a.ph;
+    const Nodes<P, Q, R> &nd = a.nd;
+    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    unsigned int oog = 0u;
+
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < a.N;
+        R cx[P], cy[P];
+        bool finished = false;
+        if (valid) {
+            load_coeffs(a, i, cx, cy);
+            // drift (Eq. (17) / sG forcing term)
+#pragma unroll
+            for (int h = 0; h < P; ++h)
+                if (nd.drift_mask & (1u << h)) {
+                    cx[h] -= nd.dhat[h];
+                    a.khat[(int64_t)h * a.ld + i] = cx[h];
+                }
+            // reconstruction, cells and the bound on the majorant
+            int cell[Q];
+            R kkmax = (R)0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                R kx, ky;
+                recon_node(nd, q, cx, cy, kx, ky);
+                cell[q] = cell_of(ph, kx, ky);
+                kkmax = fmax(kkmax, kx * kx + ky * ky);
+            }
+            const U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, 0u, a.key0, a.key1);
+            const R lnxi = -rlog<R>(u01<R>(r.x));
+            const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
+            const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
+            const bool maybe = lnxi < gub * ph.dt;
+            if (!maybe) {
+                finished = true;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    if (cell[q] >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cell[q]], 1u);
+                    else ++oog;
+                }
+            }
+            // colliders go to the queue (warp-aggregated append)
+            const unsigned int mask = __ballot_sync(__activemask(), maybe);
+            if (maybe) {
+                const int leader = __ffs(mask) - 1;
+                uint32_t basepos = 0;
+                if (lane == leader) basepos = atomicAdd(a.qcount, (uint32_t)__popc(mask));
+                basepos = __shfl_sync(mask, basepos, leader);
+                const uint32_t off = __popc(mask & ((1u << lane) - 1u));
+                a.queue[basepos + off] = (uint32_t)i;
+            }
+        }
+        if (a.out_step) {
+#pragma unroll 1
+            for (int q = 0; q < Q; ++q) {
+                float vx = 0.f, vy = 0.f, e = 0.f;
+                if (finished) {
+                    R kx, ky;
+                    recon_node(nd, q, cx, cy, kx, ky);
+                    observe(ph, kx, ky, nd.eps0[q], vx, vy, e);
+                }
+                vx = warp_sum(vx);
+                vy = warp_sum(vy);
+                e = warp_sum(e);
+                if (lane == 0) {
+                    smom[warp][q * 3 + 0] += (double)vx;
+                    smom[warp][q * 3 + 1] += (double)vy;
+                    smom[warp][q * 3 + 2] += (double)e;
+                }
+            }
+        }
+    }
+    oog = warp_sum(oog);
+    if (lane == 0 && oog) atomicAdd(&a.counters[4], (unsigned long long)oog);
+    if (a.out_step) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) s += smom[w][j];
+            a.part1[(int64_t)blockIdx.x * (Q * 3) + j] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Phase 2: the collision loop of Algorithm 1 / 2 for the queued particles.
+// ------------------------------------------------------------------------------------------
+template <int P, int Q, typename R>
+__device__ __forceinline__ R majorant(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const R *kx, const R *ky)
+{
+    R gmax = (R)0;
+#pragma unroll 1
+    for (int q = 0; q < Q; ++q) {
+        R g[6];
+        const R s = rates6(ph, kx[q], ky[q], nd.eps0[q], g);
+        gmax = fmax(gmax, s);
+    }
+    return ph.alpha1 * gmax;
+}
+
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(kPhase2Threads)
+k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
+{
+    __shared__ double smom[Q * 3];
+    __shared__ unsigned long long scnt[5];
+    if (threadIdx.x < 5) scnt[threadIdx.x] = 0ull;
+    for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) smom[j] = 0.0;
+    __syncthreads();
+
+    const Phys<R> &ph = a.ph;
+    const Nodes<P, Q, R> &nd = a.nd;
+    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    const uint32_t count = *a.qcount;
+    unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0;
+
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        const int64_t i = a.queue[j];
+        R cx[P], cy[P], kx[Q], ky[Q];
+        load_coeffs(a, i, cx, cy);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) recon_node(nd, q, cx, cy, kx[q], ky[q]);
+        R Gt = majorant(ph, nd, kx, ky);
+        R tc = (R)0;
+        uint32_t c = 0;
+        U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
+        R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(r.x)) / Gt : (R)INFINITY;
+        bool touched = false;
+        while (tc + dtc < ph.dt) {
+            if ((int)c >= ph.max_coll) { ++cap; break; }
+            ++att;
+            touched = true;
+            EventAngles<R> ang;
+            ang.reset(u01<R>(r.w));
+            const R target = u01<R>(r.y) * Gt;
+            bool changed = false;
+#pragma unroll 1
+            for (int q = 0; q < Q; ++q) {
+                R g[6];
+                rates6(ph, kx[q], ky[q], nd.eps0[q], g);
+                int l = 6;
+                R cum = (R)0;
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    cum += g[m];
+                    if (l == 6 && target < cum) l = m;
+                }
+                if (l == 6) continue;  // self scattering: h^7 = identity
+                R nkx, nky;
+                final_state(ph, l, kx[q], ky[q], nd.eps0[q], ang, &nkx, &nky);
+                bool accept = true;
+                if (ph.pauli_mode != 2) {
+                    const int cl = cell_of(ph, nkx + nd.dq[q], nky);
+                    if (cl >= 0) accept = pauli_accept(a.Hcur[(int64_t)q * NN + cl], a.nmax[q], r.z);
+                }
+                if (accept) { kx[q] = nkx; ky[q] = nky; changed = true; }
+                else ++rej;
+            }
+            if (changed) ++chg;
+            // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+                R sx = (R)0, sy = (R)0;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    sx += nd.wpsi[q * P + h] * kx[q];
+                    sy += nd.wpsi[q * P + h] * ky[q];
+                }
+                cx[h] = sx;
+                cy[h] = sy;
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) recon_node(nd, q, cx, cy, kx[q], ky[q]);
+            Gt = majorant(ph, nd, kx, ky);
+            tc += dtc;
+            ++c;
+            r = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
+            dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(r.x)) / Gt : (R)INFINITY;
+        }
+        if (touched) {
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+                a.khat[(int64_t)h * a.ld + i] = cx[h];
+                a.khat[(int64_t)(P + h) * a.ld + i] = cy[h];
+            }
+        }
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            const int cl = cell_of(ph, kx[q], ky[q]);
+            if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
+            else ++oog;
+            if (a.out_step) {
+                float vx, vy, e;
+                observe(ph, kx[q], ky[q], nd.eps0[q], vx, vy, e);
+                atomicAdd(&smom[q * 3 + 0], (double)vx);
+                atomicAdd(&smom[q * 3 + 1], (double)vy);
+                atomicAdd(&smom[q * 3 + 2], (double)e);
+            }
+        }
+    }
+    if (att) atomicAdd(&scnt[0], att);
+    if (chg) atomicAdd(&scnt[1], chg);
+    if (rej) atomicAdd(&scnt[2], rej);
+    if (cap) atomicAdd(&scnt[3], cap);
+    if (oog) atomicAdd(&scnt[4], oog);
+    __syncthreads();
+    if (threadIdx.x < 5 && scnt[threadIdx.x]) atomicAdd(&a.counters[threadIdx.x], scnt[threadIdx.x]);
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&a.counters[5], (unsigned long long)count);
+    if (a.out_step)
+        for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) a.part2[(int64_t)blockIdx.x * (Q * 3) + j] = smom[j];
+}
+
+// ------------------------------------------------------------------------------------------
+// Observation of a whole state: histogram into H and (optionally) moment partials into part1.
+// Used after the initial sampling and after a state upload.
+// ------------------------------------------------------------------------------------------
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(kPhase1Threads)
+k_observe(const __grid_constant__ StepArgs<P, Q, R> a)
+{
+    constexpr int NW = kPhase1Threads / 32;
+    __shared__ double smom[NW][Q * 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
+    const Phys<R> &ph = a.ph;
+    const Nodes<P, Q, R> &nd = a.nd;
+    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < a.N;
+        R cx[P], cy[P];
+        if (valid) load_coeffs(a, i, cx, cy);
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            float vx = 0.f, vy = 0.f, e = 0.f;
+            if (valid) {
+                R kx, ky;
+                recon_node(nd, q, cx, cy, kx, ky);
+                const int cl = cell_of(ph, kx, ky);
+                if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
+                observe(ph, kx, ky, nd.eps0[q], vx, vy, e);
+            }
+            vx = warp_sum(vx);
+            vy = warp_sum(vy);
+            e = warp_sum(e);
+            if (lane == 0) {
+                smom[warp][q * 3 + 0] += (double)vx;
+                smom[warp][q * 3 + 1] += (double)vy;
+                smom[warp][q * 3 + 2] += (double)e;
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += smom[w][j];
+        a.part1[(int64_t)blockIdx.x * (Q * 3) + j] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Initial state: Fermi-Dirac sampling at every node with shared uniforms, projection (FP64).
+// ------------------------------------------------------------------------------------------
+template <int P, int Q>
+struct InitArgs {
+    double wpsi[Q * P];
+    double eps0[Q];
+    double mu, kT, hvF;
+};
+
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(128)
+k_init(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ InitArgs<P, Q> ia)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const U4 r = philox4x32_10((uint32_t)i, a.stream_id, 0u, 0x10000u, a.key0, a.key1);
+        const double ue = u01<double>(r.x), uth = u01<double>(r.y);
+        double s, c;
+        sincos(2.0 * kPi * uth, &s, &c);
+        double hx[P], hy[P];
+#pragma unroll
+        for (int h = 0; h < P; ++h) { hx[h] = 0.0; hy[h] = 0.0; }
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            const double e0 = ia.eps0[q];
+            const double eps = fd_inverse(e0, ia.mu, ia.kT, ue);
+            const double rr = eps * eps - e0 * e0;
+            const double km = (rr > 0.0) ? sqrt(rr) / ia.hvF : 0.0;
+            const double kx = km * c, ky = km * s;
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+                hx[h] += ia.wpsi[q * P + h] * kx;
+                hy[h] += ia.wpsi[q * P + h] * ky;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            a.khat[(int64_t)h * a.ld + i] = (R)hx[h];
+            a.khat[(int64_t)(P + h) * a.ld + i] = (R)hy[h];
+        }
+    }
+}
+
+// Histogram of the particles reconstructed at one arbitrary z (Eq. (24)); psi given in FP64.
+template <int P, int Q, typename R>
+struct ReconArgs {
+    double psi[P];
+};
+
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(256)
+k_hist_at(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ ReconArgs<P, Q, R> z,
+          uint32_t *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        R kx = (R)0, ky = (R)0;
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            kx += a.khat[(int64_t)h * a.ld + i] * (R)z.psi[h];
+            ky += a.khat[(int64_t)(P + h) * a.ld + i] * (R)z.psi[h];
+        }
+        const int cl = cell_of(a.ph, kx, ky);
+        if (cl >= 0) atomicAdd(&out[cl], 1u);
+    }
+}
+
+}  // namespace pgc

@@ -1,0 +1,147 @@
+// pgc_runner_impl.cuh -- the templated Runner: fills the kernel argument blocks from the host
+// tables and launches the kernels of pgc_kernels.cuh.  Included by the per-shape instantiation
+// units so that the shapes compile in parallel.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+
+#include "pgc_kernels.cuh"
+#include "pgc_runner.h"
+
+namespace pgc {
+
+template <int P, int Q, typename R>
+class RunnerT final : public Runner {
+public:
+    RunnerT(const HostTables &t, const DevBuffers &b, int num_sms) : t_(t), b_(b)
+    {
+        fill_phys(t);
+        auto &nd = args_.nd;
+        for (int i = 0; i < Q * P; ++i) { nd.psi[i] = (R)t.psi[i]; nd.wpsi[i] = (R)t.wpsi[i]; }
+        for (int h = 0; h < P; ++h) nd.dhat[h] = (R)t.dhat[h];
+        for (int q = 0; q < Q; ++q) { nd.eps0[q] = (R)t.eps0[q]; nd.dq[q] = (R)t.dq[q]; }
+        nd.eps0_max = (R)t.eps0_max;
+        nd.drift_mask = t.drift_mask;
+        args_.khat = static_cast<R *>(b.state);
+        args_.N = b.N;
+        args_.ld = b.ld;
+        args_.hist_elems = (int64_t)Q * t.Nk * t.Nk;
+        args_.nmax = b.nmax;
+        args_.queue = b.queue;
+        args_.part1 = b.part1;
+        args_.part2 = b.part2;
+        args_.counters = b.counters;
+        args_.key0 = b.key0;
+        args_.key1 = b.key1;
+        args_.stream_id = b.stream_id;
+        for (int i = 0; i < Q * P; ++i) init_.wpsi[i] = t.wpsi[i];
+        for (int q = 0; q < Q; ++q) init_.eps0[q] = t.eps0[q];
+        init_.mu = t.mu;
+        init_.kT = t.kT;
+        init_.hvF = t.hvF;
+        // phase-1 grid: enough resident blocks to fill the GPU, at most one particle per thread
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase1<P, Q, R>, kPhase1Threads, 0);
+        per_sm = std::max(per_sm, 1);
+        const int64_t need = (b.N + kPhase1Threads - 1) / kPhase1Threads;
+        grid1_ = (int)std::max<int64_t>(1, std::min<int64_t>({need, (int64_t)num_sms * per_sm, (int64_t)kMaxGrid1}));
+    }
+
+    int grid1() const override { return grid1_; }
+
+    cudaError_t init_sample(cudaStream_t s) override
+    {
+        int blocks = (int)std::min<int64_t>((b_.N + 127) / 128, 8192);
+        k_init<P, Q, R><<<blocks, 128, 0, s>>>(args_, init_);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    cudaError_t observe(int buf, cudaStream_t s) override
+    {
+        StepArgs<P, Q, R> a = args_;
+        a.Hnext = b_.hist + (int64_t)buf * b_.hist_stride;
+        a.out_step = 1;
+        k_observe<P, Q, R><<<grid1_, kPhase1Threads, 0, s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    cudaError_t step(int64_t step, bool out_step, cudaStream_t s) override
+    {
+        StepArgs<P, Q, R> a = args_;
+        const int cur = (int)(step % 3), nxt = (int)((step + 1) % 3), clr = (int)((step + 2) % 3);
+        a.Hcur = b_.hist + (int64_t)cur * b_.hist_stride;
+        a.Hnext = b_.hist + (int64_t)nxt * b_.hist_stride;
+        a.Hclear = b_.hist + (int64_t)clr * b_.hist_stride;
+        a.qcount = b_.qcount + (step & 1);
+        a.qcount_next = b_.qcount + ((step + 1) & 1);
+        a.step = (uint32_t)step;
+        a.out_step = out_step ? 1 : 0;
+        k_phase1<P, Q, R><<<grid1_, kPhase1Threads, 0, s>>>(a);
+        k_phase2<P, Q, R><<<kGrid2, kPhase2Threads, 0, s>>>(a);
+        count_launch(2);
+        return cudaGetLastError();
+    }
+
+    cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) override
+    {
+        ReconArgs<P, Q, R> z;
+        for (int h = 0; h < P; ++h) z.psi[h] = psi[h];
+        int blocks = (int)std::min<int64_t>((b_.N + 255) / 256, 4096);
+        k_hist_at<P, Q, R><<<blocks, 256, 0, s>>>(args_, z, out);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+private:
+    void fill_phys(const HostTables &t)
+    {
+        Phys<R> &p = args_.ph;
+        p.hvF = (R)t.hvF;
+        p.hvF2 = (R)(t.hvF * t.hvF);
+        p.Lk = (R)t.Lk;
+        p.dk = (R)t.dk;
+        p.inv_dk = (R)(1.0 / t.dk);
+        p.alpha1 = (R)(1.0 + t.alpha);
+        p.dt = (R)t.dt;
+        p.Cac = (R)t.Cac;
+        p.COm = (R)(t.CO * (t.nO + 1.0));
+        p.COp = (R)(t.CO * t.nO);
+        p.CKm = (R)(t.CK * (t.nK + 1.0));
+        p.CKp = (R)(t.CK * t.nK);
+        p.hwO = (R)t.hwO;
+        p.hwK = (R)t.hwK;
+        p.wOk = (R)(t.hwO / t.hvF);
+        p.wKk = (R)(t.hwK / t.hvF);
+        p.Cedg = (R)t.Cedg;
+        p.two_a2 = (R)(2.0 * t.a_nm * t.a_nm);
+        p.edge_h = (R)(2.0 * kPi / t.n_theta);
+        p.bound_edge = (R)(2.0 * kPi * (1.0 + 1e-5));
+        p.vF_ms = (R)t.vF_ms;
+        const double h = 2.0 * kPi / t.n_theta;
+        for (int j = 0; j <= kMaxTheta; ++j) p.cosj[j] = (R)((j <= t.n_theta) ? std::cos(j * h) : 1.0);
+        p.mech = t.mech;
+        p.n_theta = t.n_theta;
+        p.pauli_mode = t.pauli_mode;
+        p.final_state = t.final_state;
+        p.max_coll = t.max_coll;
+        p.Nk = t.Nk;
+    }
+
+    HostTables t_;
+    DevBuffers b_;
+    StepArgs<P, Q, R> args_{};
+    InitArgs<P, Q> init_{};
+    int grid1_ = 1;
+};
+
+template <int P, int Q>
+Runner *make_runner_shape(int precision, const HostTables &t, const DevBuffers &b, int num_sms)
+{
+    if (precision == 1) return new RunnerT<P, Q, double>(t, b, num_sms);
+    return new RunnerT<P, Q, float>(t, b, num_sms);
+}
+
+}  // namespace pgc

@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in include/pgc.h (argument marshalling only).
+
+The functions keep the C names (pgc_query_sizes, pgc_init, pgc_step, pgc_moments,
+pgc_reconstruct_f, ...).  Every step of the particle scheme runs in the CUDA kernels of
+libpgc.so; PyTorch only provides the caller-owned device buffers and the CUDA stream.  There is
+no CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpgc.so")
+_lock = threading.Lock()
+_lib = None
+
+PGC_OK, PGC_EINVAL, PGC_ENOMEM, PGC_ECUDA, PGC_ESTATE, PGC_ETIMEOUT, PGC_EUNSUPPORTED = range(7)
+PGC_FP32, PGC_FP64 = 0, 1
+PGC_MECH_ALL = 63
+COUNTER_NAMES = ["attempts", "changed", "rejected", "capped", "out_of_grid", "queued", "error", "steps"]
+
+
+class PgcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+_STATUS = {0: "PGC_OK", 1: "PGC_EINVAL", 2: "PGC_ENOMEM", 3: "PGC_ECUDA", 4: "PGC_ESTATE",
+           5: "PGC_ETIMEOUT", 6: "PGC_EUNSUPPORTED"}
+
+
+class pgc_interval(C.Structure):
+    _fields_ = [("lo", C.c_double), ("hi", C.c_double)]
+
+
+class pgc_config(C.Structure):
+    _fields_ = [
+        ("T_K", C.c_double), ("eps_F_eV", C.c_double),
+        ("eps0_eV", pgc_interval), ("Ex_Vcm", pgc_interval),
+        ("mech_mask", C.c_uint32), ("alpha", C.c_double),
+        ("Nk", C.c_int32), ("Lk_hvF_eV", C.c_double),
+        ("degree_M", C.c_int32), ("quad_per_dim", C.c_int32),
+        ("n_particles", C.c_int64), ("dt_fs", C.c_double),
+        ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+        ("precision", C.c_int32), ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
+        ("n_theta_edge", C.c_int32), ("max_collisions", C.c_int32), ("max_outputs", C.c_int32),
+    ]
+
+
+_vp, _dp, _u32p, _u64p, _i64p = (C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
+                                 C.POINTER(C.c_uint64), C.POINTER(C.c_int64))
+
+#: exported symbols with (restype, argtypes); the header declares exactly these
+SIGNATURES = {
+    "pgc_config_default": (None, [C.POINTER(pgc_config)]),
+    "pgc_query_sizes": (C.c_int, [C.POINTER(pgc_config), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                  C.POINTER(C.c_size_t), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pgc_init": (C.c_int, [C.POINTER(pgc_config), _vp, _vp, _vp, _dp, _vp, C.POINTER(_vp)]),
+    "pgc_step": (C.c_int, [_vp, C.c_int64, C.c_int32]),
+    "pgc_moments": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _i64p]),
+    "pgc_reconstruct_f": (C.c_int, [_vp, _dp, C.c_int32, _u32p, _u32p]),
+    "pgc_get_state": (C.c_int, [_vp, _dp]),
+    "pgc_set_state": (C.c_int, [_vp, _dp]),
+    "pgc_counters": (C.c_int, [_vp, _u64p]),
+    "pgc_get_hist": (C.c_int, [_vp, _u32p, _u32p]),
+    "pgc_destroy": (None, [_vp]),
+    "pgc_last_error": (C.c_char_p, [_vp]),
+    "pgc_status_string": (C.c_char_p, [C.c_int]),
+    "pgc_launch_count": (C.c_uint64, []),
+}
+
+
+def lib():
+    """Load libpgc.so (built by paper_2404_19602_gb300.build); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libpgc.so not built (%s); run paper_2404_19602_gb300.build.build()" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != PGC_OK:
+        msg = lib().pgc_last_error(ctx)
+        raise PgcError(status, msg.decode() if msg else "")
+
+
+def _ptr(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+# ------------------------------------------------------------------------------------------
+# same-name wrappers
+# ------------------------------------------------------------------------------------------
+def pgc_config_default() -> pgc_config:
+    c = pgc_config()
+    lib().pgc_config_default(C.byref(c))
+    return c
+
+
+def pgc_query_sizes(cfg: pgc_config):
+    s, h, x = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    P, Q = C.c_int32(), C.c_int32()
+    _check(lib().pgc_query_sizes(C.byref(cfg), C.byref(s), C.byref(h), C.byref(x), C.byref(P), C.byref(Q)))
+    return dict(state_bytes=s.value, hist_bytes=h.value, scratch_bytes=x.value, P=P.value, Q=Q.value)
+
+
+def pgc_init(cfg: pgc_config, d_state: int, d_hist: int, d_scratch: int, h_init_khat=None, stream: int = 0):
+    out = _vp()
+    init = None
+    if h_init_khat is not None:
+        init = np.ascontiguousarray(h_init_khat, dtype=np.float64)
+    _check(lib().pgc_init(C.byref(cfg), _vp(d_state), _vp(d_hist), _vp(d_scratch), _ptr(init, _dp),
+                          _vp(stream), C.byref(out)))
+    return out.value
+
+
+def pgc_step(ctx, n_steps: int, moments_every: int = 0):
+    _check(lib().pgc_step(_vp(ctx), int(n_steps), int(moments_every)), _vp(ctx))
+
+
+def pgc_moments(ctx, Q: int, capacity: int):
+    T = C.c_int64()
+    t = np.zeros(capacity)
+    mean = np.zeros((capacity, 4))
+    var = np.zeros((capacity, 4))
+    nodes = np.zeros((capacity, Q, 4))
+    _check(lib().pgc_moments(_vp(ctx), _ptr(t, _dp), _ptr(mean, _dp), _ptr(var, _dp), _ptr(nodes, _dp),
+                             C.byref(T)), _vp(ctx))
+    n = T.value
+    return dict(t_fs=t[:n], mean=mean[:n], var=var[:n], nodes=nodes[:n])
+
+
+def pgc_reconstruct_f(ctx, z, d: int, Nk: int):
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.float64).reshape(-1, max(d, 1)))
+    nz = z.shape[0]
+    H = np.zeros((nz, Nk, Nk), dtype=np.uint32)
+    m = np.zeros(nz, dtype=np.uint32)
+    _check(lib().pgc_reconstruct_f(_vp(ctx), _ptr(z, _dp), nz, _ptr(H, _u32p), _ptr(m, _u32p)), _vp(ctx))
+    return H, m
+
+
+def pgc_get_state(ctx, P: int, N: int):
+    a = np.zeros((2, P, N))
+    _check(lib().pgc_get_state(_vp(ctx), _ptr(a, _dp)), _vp(ctx))
+    return a
+
+
+def pgc_set_state(ctx, khat):
+    a = np.ascontiguousarray(khat, dtype=np.float64)
+    _check(lib().pgc_set_state(_vp(ctx), _ptr(a, _dp)), _vp(ctx))
+
+
+def pgc_counters(ctx):
+    a = np.zeros(8, dtype=np.uint64)
+    _check(lib().pgc_counters(_vp(ctx), _ptr(a, _u64p)), _vp(ctx))
+    return dict(zip(COUNTER_NAMES, [int(x) for x in a]))
+
+
+def pgc_get_hist(ctx, Q: int, Nk: int):
+    H = np.zeros((Q, Nk, Nk), dtype=np.uint32)
+    m = np.zeros(Q, dtype=np.uint32)
+    _check(lib().pgc_get_hist(_vp(ctx), _ptr(H, _u32p), _ptr(m, _u32p)), _vp(ctx))
+    return H, m
+
+
+def pgc_destroy(ctx):
+    if ctx:
+        lib().pgc_destroy(_vp(ctx))
+
+
+def pgc_launch_count() -> int:
+    return int(lib().pgc_launch_count())
+
+
+# ------------------------------------------------------------------------------------------
+# configuration from a workload dictionary (paper_2404_19602_gb300.workloads)
+# ------------------------------------------------------------------------------------------
+def config_from(params: dict, max_outputs: int = 1024) -> pgc_config:
+    c = pgc_config_default()
+    p = params
+    c.T_K = p.get("T_K", c.T_K)
+    c.eps_F_eV = p.get("eps_F", c.eps_F_eV)
+    c.eps0_eV.lo = p.get("eps0_lo", c.eps0_eV.lo)
+    c.eps0_eV.hi = p.get("eps0_hi", c.eps0_eV.hi)
+    c.Ex_Vcm.lo = p.get("Ex_lo", c.Ex_Vcm.lo)
+    c.Ex_Vcm.hi = p.get("Ex_hi", c.Ex_Vcm.hi)
+    c.mech_mask = p.get("mech_mask", c.mech_mask)
+    c.alpha = p.get("alpha", c.alpha)
+    c.Nk = p.get("Nk", c.Nk)
+    c.Lk_hvF_eV = p.get("Lk_hvF", c.Lk_hvF_eV)
+    c.degree_M = p.get("M", c.degree_M)
+    c.quad_per_dim = p.get("Q1", c.quad_per_dim)
+    c.n_particles = p.get("N", c.n_particles)
+    c.dt_fs = p.get("dt_fs", c.dt_fs)
+    c.seed = p.get("seed", c.seed)
+    c.stream_id = p.get("stream_id", c.stream_id)
+    prec = p.get("precision", "fp32")
+    c.precision = PGC_FP64 if prec in ("fp64", 1) else PGC_FP32
+    c.pauli_norm = p.get("pauli_norm", c.pauli_norm)
+    c.final_state = p.get("final_state", c.final_state)
+    c.n_theta_edge = p.get("n_theta", c.n_theta_edge)
+    c.max_collisions = p.get("max_coll", c.max_collisions)
+    c.max_outputs = max_outputs
+    return c
+
+
+class Simulation:
+    """One ensemble on the current CUDA device; device buffers are torch tensors.
+
+    >>> sim = Simulation(workloads.GAP_UQ_1E6)
+    >>> sim.step(5000, moments_every=10)
+    >>> m = sim.moments()       # t_fs, mean/var of (Vx, Vy, energy, Jx), per-node values
+    """
+
+    def __init__(self, params: dict, init_khat=None, max_outputs: int = 1024, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.params = dict(params)
+        self.cfg = config_from(params, max_outputs)
+        sz = pgc_query_sizes(self.cfg)
+        self.P, self.Q = sz["P"], sz["Q"]
+        self.N = int(self.cfg.n_particles)
+        self.Nk = int(self.cfg.Nk)
+        self.d = int(self.cfg.eps0_eV.lo != self.cfg.eps0_eV.hi) + int(self.cfg.Ex_Vcm.lo != self.cfg.Ex_Vcm.hi)
+        self.max_outputs = max_outputs
+        dev = torch.device("cuda", torch.cuda.current_device())
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.state_buf = torch.empty(sz["state_bytes"], dtype=torch.uint8, device=dev)
+        self.hist_buf = torch.empty(sz["hist_bytes"], dtype=torch.uint8, device=dev)
+        self.scratch_buf = torch.empty(sz["scratch_bytes"], dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ctx = pgc_init(self.cfg, self.state_buf.data_ptr(), self.hist_buf.data_ptr(),
+                            self.scratch_buf.data_ptr(), init_khat, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pgc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_steps: int, moments_every: int = 0):
+        pgc_step(self.ctx, n_steps, moments_every)
+
+    def moments(self):
+        return pgc_moments(self.ctx, self.Q, self.max_outputs)
+
+    def state(self):
+        return pgc_get_state(self.ctx, self.P, self.N)
+
+    def set_state(self, khat):
+        pgc_set_state(self.ctx, khat)
+
+    def counters(self):
+        return pgc_counters(self.ctx)
+
+    def hist(self):
+        return pgc_get_hist(self.ctx, self.Q, self.Nk)
+
+    def reconstruct_f(self, z):
+        return pgc_reconstruct_f(self.ctx, z, self.d, self.Nk)

@@ -1,0 +1,96 @@
+"""The C-ABI library loads and exports every entry point include/pgc.h declares; configuration
+checks run on the host (no GPU needed).  Also checks that the oracle and the CUDA library share
+no code."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2404_19602_gb300 import build, pgc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return pgc.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pgc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pgc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "pgc_init" in names and "pgc_step" in names and "pgc_moments" in names
+    assert "pgc_reconstruct_f" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in pgc.SIGNATURES, n
+
+
+def test_query_sizes_default(lib):
+    cfg = pgc.pgc_config_default()
+    s = pgc.pgc_query_sizes(cfg)
+    assert s["P"] == 1 and s["Q"] == 1
+    assert s["state_bytes"] == 2 * 1 * 10048 * 4
+    assert s["hist_bytes"] >= 3 * 240 * 240 * 4
+
+
+def test_query_sizes_gpc_shapes(lib):
+    from paper_2404_19602_gb300 import workloads as W
+
+    s = pgc.pgc_query_sizes(pgc.config_from(W.GAP_UQ_1E6))
+    assert (s["P"], s["Q"]) == (6, 6)
+    assert s["state_bytes"] == 2 * 6 * 1_000_000 * 4
+    s = pgc.pgc_query_sizes(pgc.config_from(W.GAP_FIELD_UQ_4E6))
+    assert (s["P"], s["Q"]) == (21, 36)
+    s = pgc.pgc_query_sizes(pgc.config_from(W.scaled(W.GAP_UQ_1E6, precision="fp64")))
+    assert s["state_bytes"] == 2 * 6 * 1_000_000 * 8
+
+
+@pytest.mark.parametrize("field,value", [("n_particles", 0), ("dt_fs", 0.0), ("Nk", 1), ("precision", 7),
+                                         ("pauli_norm", 5), ("n_theta_edge", 63), ("mech_mask", 64),
+                                         ("max_outputs", 0)])
+def test_invalid_configs_are_rejected(lib, field, value):
+    cfg = pgc.pgc_config_default()
+    setattr(cfg, field, value)
+    with pytest.raises(pgc.PgcError) as e:
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EINVAL
+    assert lib.pgc_last_error(None)
+
+
+def test_uncompiled_shape_is_unsupported(lib):
+    cfg = pgc.pgc_config_default()
+    cfg.eps0_eV.lo, cfg.eps0_eV.hi = 0.05, 0.15
+    cfg.degree_M, cfg.quad_per_dim = 3, 4
+    with pytest.raises(pgc.PgcError) as e:
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EUNSUPPORTED
+
+
+def test_init_rejects_null_buffers(lib):
+    cfg = pgc.pgc_config_default()
+    out = C.c_void_p()
+    st = lib.pgc_init(C.byref(cfg), None, None, None, None, None, C.byref(out))
+    assert st == pgc.PGC_EINVAL and not out.value
+
+
+def test_oracle_and_library_share_no_code():
+    pkg = os.path.join(ROOT, "paper_2404_19602_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "pgc_oracle" not in txt, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2404_19602_gb300" not in txt, f
+            assert "pgc.h" not in txt and "csrc" not in txt, f

@@ -1,0 +1,182 @@
+"""CUDA library vs the FP64 CPU oracle, element by element on the same seeded inputs.
+
+All calls go through the C ABI (paper_2404_19602_gb300.pgc).  Tolerances:
+  * FP64 mode: the kernels take the same discrete decisions as the oracle; states agree to
+    rounding (<= 1e-9 relative per particle) and moments to <= 1e-9 normwise, far inside the
+    1e-3 bound of the moment comparison;
+  * pure drift (mechanisms off) in FP64: <= 1e-10 per particle;
+  * FP32 state: moments within 1e-3 normwise (|a(t)-b(t)| / max_t |b|) on short horizons.
+    FP32 rounding occasionally moves a node value across a cell edge or a selection threshold;
+    through the shared Pauli histogram such a difference spreads to other particles, so the
+    per-particle comparison counts the diverged particles instead of requiring all to agree.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_19602_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_19602_gb300 import build
+
+    build.build()
+    O.build()
+
+
+def _pgc():
+    from paper_2404_19602_gb300 import pgc
+
+    return pgc
+
+
+def _normwise(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def _compare_moments(g, r, tol, comps=(0, 2, 3), var=True):
+    assert g["mean"].shape == r["mean"].shape
+    assert np.allclose(g["t_fs"], r["t_fs"])
+    worst = 0.0
+    for comp in comps:
+        e = _normwise(g["mean"][:, comp], r["mean"][:, comp])
+        worst = max(worst, e)
+        assert e <= tol, ("mean", comp, e)
+        if var and np.abs(r["var"][:, comp]).max() > 0:
+            e = _normwise(g["var"][:, comp], r["var"][:, comp])
+            worst = max(worst, e)
+            assert e <= tol, ("var", comp, e)
+    return worst
+
+
+def _run_pair(p, steps, every, init_from_oracle=False):
+    pgc = _pgc()
+    o = O.Oracle(p)
+    init = o.state() if init_from_oracle else None
+    sim = pgc.Simulation(p, init_khat=init, max_outputs=steps // every + 2)
+    sim.step(steps, every)
+    o.step(steps, every)
+    return sim, o
+
+
+@pytest.mark.parametrize("shape", ["det", "gap", "gap_field"])
+def test_initial_sampling_matches_oracle(shape):
+    base = {"det": W.DET_FP64_1E4, "gap": W.GAP_UQ_1E6, "gap_field": W.GAP_FIELD_UQ_4E6}[shape]
+    p = W.scaled(base, N=777 if shape == "gap_field" else 4099, precision="fp64")
+    pgc = _pgc()
+    sim = pgc.Simulation(p)
+    g = sim.state()
+    r = O.Oracle(p).state()
+    assert np.abs(g - r).max() <= 1e-9 * np.abs(r).max()
+    Hg, mg = sim.hist()
+    Hr, mr = O.Oracle(p).hist()
+    assert np.array_equal(mg, mr)
+    assert np.abs(Hg.astype(np.int64) - Hr.astype(np.int64)).sum() <= 2 * sim.Q  # cell-edge ties only
+
+
+def test_pure_drift_fp64_per_particle():
+    p = W.scaled(W.DET_FP64_1E4, mech_mask=0)
+    sim, o = _run_pair(p, 2000, 100, init_from_oracle=True)
+    g, r = sim.state(), o.state()
+    assert np.abs(g - r).max() <= 1e-10 * np.abs(r).max()
+    _compare_moments(sim.moments(), o.moments(), 1e-10)
+
+
+def test_pure_drift_random_field_fp64():
+    p = W.scaled(W.GAP_FIELD_UQ_4E6, N=1000, mech_mask=0, precision="fp64")
+    sim, o = _run_pair(p, 500, 50, init_from_oracle=True)
+    g, r = sim.state(), o.state()
+    assert np.abs(g - r).max() <= 1e-10 * np.abs(r).max()
+
+
+def test_deterministic_fp64_full_size():
+    """Deterministic inputs, 1e4 particles, 2000 steps of 1 fs, FP64 (Algorithm 1)."""
+    p = W.DET_FP64_1E4
+    sim, o = _run_pair(p, p["steps"], 10)
+    worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+    assert worst <= 1e-9, worst
+    g, r = sim.state(), o.state()
+    diverged = (np.abs(g - r).max(axis=(0, 1)) > 1e-8).sum()
+    assert diverged <= 2, diverged
+    cg, cr = sim.counters(), o.counters()
+    assert cg["attempts"] == cr["attempts"]
+    assert cg["rejected"] == cr["rejected"]
+
+
+def test_gap_uq_fp64_elementwise():
+    p = W.scaled(W.GAP_UQ_1E6, N=20000, precision="fp64")
+    sim, o = _run_pair(p, 300, 10)
+    worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+    assert worst <= 1e-8, worst
+    g, r = sim.state(), o.state()
+    diverged = (np.abs(g - r).max(axis=(0, 1)) > 1e-8).sum()
+    assert diverged <= 2, diverged
+
+
+def test_gap_uq_fp32_moments():
+    p = W.scaled(W.GAP_UQ_1E6, N=20000)
+    sim, o = _run_pair(p, 100, 10)
+    _compare_moments(sim.moments(), o.moments(), 1e-3)
+    g, r = sim.state(), o.state()
+    diverged = (np.abs(g - r).max(axis=(0, 1)) > 1e-4).sum()
+    assert diverged <= 0.002 * p["N"], diverged
+
+
+def test_gap_field_uq_fp64_elementwise():
+    p = W.scaled(W.GAP_FIELD_UQ_4E6, N=3000, precision="fp64")
+    sim, o = _run_pair(p, 60, 10)
+    worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+    assert worst <= 1e-8, worst
+
+
+def test_gap_field_uq_fp32_moments():
+    p = W.scaled(W.GAP_FIELD_UQ_4E6, N=3000)
+    sim, o = _run_pair(p, 40, 10)
+    _compare_moments(sim.moments(), o.moments(), 1e-3)
+
+
+@pytest.mark.parametrize("N", [1, 33, 257, 65 * 64 + 3])
+def test_ragged_sizes_fp64(N):
+    p = W.scaled(W.GAP_UQ_1E6, N=N, precision="fp64")
+    sim, o = _run_pair(p, 30, 10)
+    g, r = sim.state(), o.state()
+    assert np.abs(g - r).max() <= 1e-9 * max(np.abs(r).max(), 1.0)
+
+
+def test_conservation_and_histogram_match():
+    p = W.scaled(W.GAP_UQ_1E6, N=5000, precision="fp64")
+    sim, o = _run_pair(p, 50, 10)
+    Hg, _ = sim.hist()
+    Hr, _ = o.hist()
+    assert np.abs(Hg.astype(np.int64) - Hr.astype(np.int64)).sum() <= 2 * sim.Q
+    c = sim.counters()
+    assert int(Hg.sum()) <= p["N"] * sim.Q
+    z = np.linspace(-1, 1, 5)
+    Zg, mg = sim.reconstruct_f(z)
+    Zr, mr = o.reconstruct_f(z)
+    assert np.abs(Zg.astype(np.int64) - Zr.astype(np.int64)).sum() <= 2 * len(z)
+    assert np.abs(mg.astype(np.int64) - mr.astype(np.int64)).max() <= 1
+    assert c["steps"] == 50
+
+
+def test_pauli_modes_fp64():
+    for mode in (1, 2):
+        p = W.scaled(W.DET_FP64_1E4, N=5000, pauli_norm=mode)
+        sim, o = _run_pair(p, 200, 20)
+        worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+        assert worst <= 1e-8, (mode, worst)
+
+
+def test_exact_energy_final_state_fp64():
+    p = W.scaled(W.DET_FP64_1E4, N=5000, final_state=1)
+    sim, o = _run_pair(p, 200, 20)
+    worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+    assert worst <= 1e-8, worst
