@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput of the particle stochastic-Galerkin time step (arXiv:2404.19602) on GB300.
+
+A bench "step" advances the whole ensemble by --time-steps time steps (default 500 of 1 fs);
+the default K = 10 timed steps are one full run of the workload (5000 time steps) from the
+Fermi-Dirac state.  Metric: particle-gPC-steps/s = particles x time steps / device time.
+L2 is flushed (a 256 MiB write) between timed steps; within a step the ensemble state of the
+default workload (48 MB) stays L2-resident across its time steps, as in any run of that size.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload gap_uq|det|gap_field]
+  python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Under torchrun (N > 1) each rank advances its own independent ensemble (stream_id = rank):
+the particle ensembles of a batch of cases need no exchange (weak scaling), and the timing is
+the maximum over ranks.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2404_19602_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6}
+METRIC = "particle-gPC-steps/s"
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pgc", choices=["pgc", "reference"])
+    ap.add_argument("--workload", default="gap_uq", choices=sorted(WORKLOADS))
+    ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
+    ap.add_argument("--moments-every", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + SMI_FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _src_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2404_19602_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[workload][kernel]
+        if e.get("src_sha") != _src_sha():
+            return None
+        return e["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def cpu_baseline(p):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    import oracle as O
+
+    O.build()
+    n, steps = (20000, 300) if p["M"] and p["Q1"] <= 6 and p["eps0_lo"] != p["eps0_hi"] and p["Ex_lo"] == p["Ex_hi"] else (
+        (10000, 400) if p["eps0_lo"] == p["eps0_hi"] else (2000, 40))
+    q = W.scaled(p, N=n)
+    o = O.Oracle(q)
+    t0 = time.perf_counter()
+    o.step(steps, p.get("moments_every", 10))
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d particles x %d time steps of the same workload (FP64, OpenMP)" % (n, steps),
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    p = WORKLOADS[args.workload]
+    n = 20000 if p["N"] >= 1_000_000 and p["Q1"] <= 6 else (10000 if p["N"] <= 10000 else 2000)
+    S = 20 if p["Q1"] <= 6 else 4
+    q = W.scaled(p, N=n)
+    o = O.Oracle(q)
+    for _ in range(args.warmup):
+        o.step(S, args.moments_every)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(S, args.moments_every)
+    dt = time.perf_counter() - t0
+    value = n * S * args.steps / dt
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": p["name"], "sample_particles": n, "time_steps_per_step": S,
+                   "note": "FP64 CPU oracle (C, OpenMP) on a bounded sample of the workload"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": "%d particles x %d time steps per step" % (n, S)},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_19602_gb300 import pgc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2404_19602_gb300 import build as B
+
+    B.build()
+    p = W.scaled(WORKLOADS[args.workload], stream_id=rank)
+    S, K = args.time_steps, args.steps
+    every = args.moments_every
+    cap = (K + args.warmup) * S // max(every, 1) + 8
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up on a separate instance (module load, first launches, clocks)
+    warm = pgc.Simulation(p, max_outputs=cap)
+    for _ in range(args.warmup):
+        warm.step(S, every)
+    torch.cuda.synchronize()
+    warm.close()
+    del warm
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sim = pgc.Simulation(p, max_outputs=cap)
+    pgc.pgc_profile(sim.ctx, 10)
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = pgc.pgc_launch_count()
+    barrier()
+    w0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))                    # evict L2 between timed steps (not timed)
+        ev[k][0].record(stream)
+        sim.step(S, every)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - w0
+    launches = pgc.pgc_launch_count() - launches0
+    clk = clocks.stop()
+    gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = pgc.pgc_profile_read(sim.ctx)
+    cnt = sim.counters()
+    t = torch.tensor([gpu_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    gpu_ms_max = float(t.item())
+    N = p["N"]
+    value = N * world * S * K / (gpu_ms_max / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    P, Q = sim.P, sim.Q
+    esz = 8 if p.get("precision") == "fp64" else 4
+    n_drift = 1 if p["Ex_lo"] == p["Ex_hi"] else 2
+    queued = cnt["queued"] / max(cnt["steps"], 1)
+    bytes1 = N * (2 * P * esz + n_drift * esz)          # read the state, write the drifted coefficients
+    bytes2 = queued * (2 * (2 * P * esz) + 4)           # colliders: read + write the state, queue index
+    peak, peak_kind = _peaks()
+    dominant = "k_phase1" if prof["phase1_ms"] >= prof["phase2_ms"] else "k_phase2"
+    ms_dom = max(prof["phase1_ms"], prof["phase2_ms"])
+    by = bytes1 if dominant == "k_phase1" else bytes2
+    achieved = by / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic(dominant, args.workload),
+                "kernel": dominant, "peak_source": peak_kind,
+                "phase1_ms": prof["phase1_ms"], "phase2_ms": prof["phase2_ms"],
+                "bytes_per_launch": by, "samples": prof["samples"]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_state = sim.state()
+        sim.close()
+        sim2 = pgc.Simulation(p, max_outputs=cap)
+        barrier()
+        e0 = time.perf_counter()
+        for k in range(K):
+            sim2.set_state(host_state)               # H2D of the step's input state (pinned staging)
+            sim2.step(S, every)
+            m = sim2.moments()                       # D2H of the moment series (synchronizes)
+        barrier()
+        e_dt = time.perf_counter() - e0
+        te = torch.tensor([e_dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        state_bytes = pgc.pgc_query_sizes(sim2.cfg)["state_bytes"]
+        e2e = {"value": N * world * S * K / float(te.item()), "unit": METRIC,
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": int(m["t_fs"].size * (1 + 4 * Q + 8) * 8)}
+        sim2.close()
+    else:
+        sim.close()
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(p)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": gpu_ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if p.get("precision") == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": p["name"], "particles_per_gpu": N, "P": P, "Q": Q,
+                       "time_steps_per_step": S, "dt_fs": p["dt_fs"], "moments_every": every,
+                       "l2": "flushed (256 MiB write) between timed steps; the state stays L2-resident "
+                             "across the time steps of one step when it fits",
+                       "parallelism": "independent ensembles per GPU" if world > 1 else "1 GPU"},
+            "roofline": roofline,
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": wall,
+            "collisions_per_step": cnt["attempts"] / max(cnt["steps"], 1),
+            "queued_per_step": queued,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,14 @@ pgc_status pgc_counters(pgc_ctx *ctx, uint64_t *h_counters);
 /* Current histogram f^n: h_hist[Q][Nk][Nk] and the normaliser Nmax[Q] of the Pauli test. */
 pgc_status pgc_get_hist(pgc_ctx *ctx, uint32_t *h_hist, uint32_t *h_nmax);
 
+/* Kernel timing samples (tracing): with every > 0, CUDA events are recorded on the context
+ * stream around the two kernels of every `every`-th step; every = 0 switches it off and
+ * clears the samples.  pgc_profile_read (synchronizes) returns the mean duration in ms of the
+ * streaming kernel (phase 1: drift, reconstruction, flight-time screen, histogram) and of the
+ * collider kernel (phase 2: collision loop of Algorithms 1/2) over the samples. */
+pgc_status pgc_profile(pgc_ctx *ctx, int32_t every);
+pgc_status pgc_profile_read(pgc_ctx *ctx, double *ms_phase1, double *ms_phase2, int64_t *samples);
+
 /* Release the context (does not free the caller's buffers). NULL is a no-op. */
 void pgc_destroy(pgc_ctx *ctx);
 

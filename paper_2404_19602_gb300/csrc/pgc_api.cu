@@ -306,7 +306,41 @@ struct pgc_ctx {
     uint32_t *tmp_max = nullptr;
     bool failed = false;
     std::string err;
+    // kernel timing samples (pgc_profile): events around phase 1 / phase 2 of sampled steps
+    int prof_every = 0;
+    std::vector<cudaEvent_t> prof_ev;  // 3 per sample
+    int prof_used = 0;
+    double prof_ms[2] = {0.0, 0.0};
+    int64_t prof_samples = 0;
+    // pinned host staging buffer of the state transfers (allocated on first use)
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
 };
+
+static void *staging(pgc_ctx *ctx, size_t bytes)
+{
+    if (ctx->pinned_bytes >= bytes) return ctx->pinned;
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    if (cudaMallocHost(&ctx->pinned, bytes) != cudaSuccess) { ctx->pinned = nullptr; return nullptr; }
+    ctx->pinned_bytes = bytes;
+    return ctx->pinned;
+}
+
+static void prof_collect(pgc_ctx *ctx)
+{
+    for (int k = 0; k < ctx->prof_used; ++k) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, ctx->prof_ev[3 * k], ctx->prof_ev[3 * k + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ctx->prof_ev[3 * k + 1], ctx->prof_ev[3 * k + 2]) == cudaSuccess) {
+            ctx->prof_ms[0] += a;
+            ctx->prof_ms[1] += b;
+            ctx->prof_samples++;
+        }
+    }
+    ctx->prof_used = 0;
+}
 
 static std::mutex g_err_mu;
 static std::string g_err;
@@ -558,7 +592,16 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
             k_hist_max<<<ctx->t.Q, 256, 0, s>>>(ctx->b.hist + (int64_t)(n % 3) * ctx->b.hist_stride, cells, ctx->b.nmax);
             count_launch();
         }
-        cudaError_t e = ctx->run->step(n, out, s);
+        cudaEvent_t *ev = nullptr;
+        if (ctx->prof_every > 0 && (n % ctx->prof_every) == 0) {
+            if (ctx->prof_used * 3 + 3 > (int)ctx->prof_ev.size()) {
+                cudaError_t se = cudaStreamSynchronize(s);
+                if (se != cudaSuccess) return cuda_fail(ctx, se, "profile sync");
+                prof_collect(ctx);
+            }
+            ev = &ctx->prof_ev[(size_t)3 * ctx->prof_used++];
+        }
+        cudaError_t e = ctx->run->step(n, out, s, ev);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
         ctx->step = n + 1;
         if (out) {
@@ -603,14 +646,16 @@ pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat)
     const int64_t N = ctx->b.N, ld = ctx->b.ld;
     const bool f64 = ctx->cfg.precision == PGC_FP64;
     const size_t esz = f64 ? 8 : 4;
-    std::vector<char> tmp((size_t)2 * P * ld * esz);
-    cudaError_t e = cudaMemcpyAsync(tmp.data(), ctx->b.state, tmp.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    const size_t bytes = (size_t)2 * P * ld * esz;
+    char *tmp = (char *)staging(ctx, bytes);
+    if (!tmp) return fail(ctx, PGC_ENOMEM, "pinned staging buffer");
+    cudaError_t e = cudaMemcpyAsync(tmp, ctx->b.state, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
     for (int p = 0; p < 2 * P; ++p)
         for (int64_t i = 0; i < N; ++i)
-            h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp.data())[(size_t)p * ld + i]
-                                            : (double)((const float *)tmp.data())[(size_t)p * ld + i];
+            h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp)[(size_t)p * ld + i]
+                                            : (double)((const float *)tmp)[(size_t)p * ld + i];
     return PGC_OK;
 }
 
@@ -622,14 +667,23 @@ pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
     const int64_t N = ctx->b.N, ld = ctx->b.ld;
     const bool f64 = ctx->cfg.precision == PGC_FP64;
     const size_t esz = f64 ? 8 : 4;
-    std::vector<char> tmp((size_t)2 * P * ld * esz, 0);
-    for (int p = 0; p < 2 * P; ++p)
+    const size_t bytes = (size_t)2 * P * ld * esz;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);  // the staging buffer may still be in use
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync");
+    char *tmp = (char *)staging(ctx, bytes);
+    if (!tmp) return fail(ctx, PGC_ENOMEM, "pinned staging buffer");
+    for (int p = 0; p < 2 * P; ++p) {
         for (int64_t i = 0; i < N; ++i) {
             const double v = h_khat[(size_t)p * N + i];
-            if (f64) ((double *)tmp.data())[(size_t)p * ld + i] = v;
-            else ((float *)tmp.data())[(size_t)p * ld + i] = (float)v;
+            if (f64) ((double *)tmp)[(size_t)p * ld + i] = v;
+            else ((float *)tmp)[(size_t)p * ld + i] = (float)v;
         }
-    cudaError_t e = cudaMemcpyAsync(ctx->b.state, tmp.data(), tmp.size(), cudaMemcpyHostToDevice, ctx->stream);
+        for (int64_t i = N; i < ld; ++i) {
+            if (f64) ((double *)tmp)[(size_t)p * ld + i] = 0.0;
+            else ((float *)tmp)[(size_t)p * ld + i] = 0.0f;
+        }
+    }
+    e = cudaMemcpyAsync(ctx->b.state, tmp, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
     // the histogram of the uploaded state becomes f^n (the Pauli normaliser is kept)
@@ -696,9 +750,42 @@ pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32
     return PGC_OK;
 }
 
+pgc_status pgc_profile(pgc_ctx *ctx, int32_t every)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (every < 0) return fail(ctx, PGC_EINVAL, "every < 0");
+    if (every > 0 && ctx->prof_ev.empty()) {
+        ctx->prof_ev.resize(3 * 256);
+        for (auto &ev : ctx->prof_ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "event create");
+        }
+    }
+    ctx->prof_every = every;
+    ctx->prof_used = 0;
+    ctx->prof_ms[0] = ctx->prof_ms[1] = 0.0;
+    ctx->prof_samples = 0;
+    return PGC_OK;
+}
+
+pgc_status pgc_profile_read(pgc_ctx *ctx, double *ms_phase1, double *ms_phase2, int64_t *samples)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile sync");
+    prof_collect(ctx);
+    const double n = ctx->prof_samples > 0 ? (double)ctx->prof_samples : 1.0;
+    if (ms_phase1) *ms_phase1 = ctx->prof_ms[0] / n;
+    if (ms_phase2) *ms_phase2 = ctx->prof_ms[1] / n;
+    if (samples) *samples = ctx->prof_samples;
+    return PGC_OK;
+}
+
 void pgc_destroy(pgc_ctx *ctx)
 {
     if (!ctx) return;
+    for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx->run;
     delete ctx;
 }

@@ -89,14 +89,15 @@ __device__ __forceinline__ void recon_node(const Nodes<P, Q, R> &nd, int q, cons
     ky = sy;
 }
 
-// group velocity (units of vF) and energy at one node (Sec. 2)
+// group velocity (units of vF) and energy at one node (Sec. 2).  The warp partial sums are
+// taken in R (FP32 in the production mode, FP64 in the FP64 mode) and accumulated in FP64.
 template <typename R>
-__device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, float &vx, float &vy, float &e)
+__device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, R &vx, R &vy, R &e)
 {
     const R eps = rsqrt_<R>(ph.hvF2 * (kx * kx + ky * ky) + eps0 * eps0);
-    vx = (float)(ph.hvF * kx / eps);
-    vy = (float)(ph.hvF * ky / eps);
-    e = (float)eps;
+    vx = ph.hvF * kx / eps;
+    vy = ph.hvF * ky / eps;
+    e = eps;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -180,7 +181,7 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
         if (a.out_step) {
 #pragma unroll 1
             for (int q = 0; q < Q; ++q) {
-                float vx = 0.f, vy = 0.f, e = 0.f;
+                R vx = (R)0, vy = (R)0, e = (R)0;
                 if (finished) {
                     R kx, ky;
                     recon_node(nd, q, cx, cy, kx, ky);
@@ -318,7 +319,7 @@ k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
             if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
             else ++oog;
             if (a.out_step) {
-                float vx, vy, e;
+                R vx, vy, e;
                 observe(ph, kx[q], ky[q], nd.eps0[q], vx, vy, e);
                 atomicAdd(&smom[q * 3 + 0], (double)vx);
                 atomicAdd(&smom[q * 3 + 1], (double)vy);
@@ -360,7 +361,7 @@ k_observe(const __grid_constant__ StepArgs<P, Q, R> a)
         if (valid) load_coeffs(a, i, cx, cy);
 #pragma unroll 1
         for (int q = 0; q < Q; ++q) {
-            float vx = 0.f, vy = 0.f, e = 0.f;
+            R vx = (R)0, vy = (R)0, e = (R)0;
             if (valid) {
                 R kx, ky;
                 recon_node(nd, q, cx, cy, kx, ky);

@@ -55,8 +55,9 @@ public:
     virtual cudaError_t init_sample(cudaStream_t s) = 0;
     // histogram of the current state into hist buffer `buf` and moment partials into part1
     virtual cudaError_t observe(int buf, cudaStream_t s) = 0;
-    // time step number `step` (histograms rotate over the three buffers)
-    virtual cudaError_t step(int64_t step, bool out_step, cudaStream_t s) = 0;
+    // time step number `step` (histograms rotate over the three buffers); if ev is non-NULL,
+    // ev[0..2] are recorded before phase 1, between the phases and after phase 2
+    virtual cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev = nullptr) = 0;
     // histogram at one arbitrary z (psi of length P, FP64) into out [Nk*Nk]
     virtual cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) = 0;
 };

@@ -68,7 +68,7 @@ public:
         return cudaGetLastError();
     }
 
-    cudaError_t step(int64_t step, bool out_step, cudaStream_t s) override
+    cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev) override
     {
         StepArgs<P, Q, R> a = args_;
         const int cur = (int)(step % 3), nxt = (int)((step + 1) % 3), clr = (int)((step + 2) % 3);
@@ -79,8 +79,11 @@ public:
         a.qcount_next = b_.qcount + ((step + 1) & 1);
         a.step = (uint32_t)step;
         a.out_step = out_step ? 1 : 0;
+        if (ev) cudaEventRecord(ev[0], s);
         k_phase1<P, Q, R><<<grid1_, kPhase1Threads, 0, s>>>(a);
+        if (ev) cudaEventRecord(ev[1], s);
         k_phase2<P, Q, R><<<kGrid2, kPhase2Threads, 0, s>>>(a);
+        if (ev) cudaEventRecord(ev[2], s);
         count_launch(2);
         return cudaGetLastError();
     }

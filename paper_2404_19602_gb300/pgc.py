@@ -68,6 +68,8 @@ SIGNATURES = {
     "pgc_set_state": (C.c_int, [_vp, _dp]),
     "pgc_counters": (C.c_int, [_vp, _u64p]),
     "pgc_get_hist": (C.c_int, [_vp, _u32p, _u32p]),
+    "pgc_profile": (C.c_int, [_vp, C.c_int32]),
+    "pgc_profile_read": (C.c_int, [_vp, _dp, _dp, _i64p]),
     "pgc_destroy": (None, [_vp]),
     "pgc_last_error": (C.c_char_p, [_vp]),
     "pgc_status_string": (C.c_char_p, [C.c_int]),
@@ -174,6 +176,16 @@ def pgc_get_hist(ctx, Q: int, Nk: int):
     m = np.zeros(Q, dtype=np.uint32)
     _check(lib().pgc_get_hist(_vp(ctx), _ptr(H, _u32p), _ptr(m, _u32p)), _vp(ctx))
     return H, m
+
+
+def pgc_profile(ctx, every: int):
+    _check(lib().pgc_profile(_vp(ctx), int(every)), _vp(ctx))
+
+
+def pgc_profile_read(ctx):
+    a, b, n = C.c_double(), C.c_double(), C.c_int64()
+    _check(lib().pgc_profile_read(_vp(ctx), C.byref(a), C.byref(b), C.byref(n)), _vp(ctx))
+    return dict(phase1_ms=a.value, phase2_ms=b.value, samples=n.value)
 
 
 def pgc_destroy(ctx):
