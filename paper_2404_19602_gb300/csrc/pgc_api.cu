@@ -13,7 +13,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/pgc.h"
+#include "pgc.h"
 #include "pgc_device.cuh"
 #include "pgc_kernels.cuh"
 #include "pgc_runner.h"
@@ -205,7 +205,7 @@ static void build_tables(const pgc_config &c, HostTables &t)
         t.eps0[q] = er ? c.eps0_eV.lo + 0.5 * (c.eps0_eV.hi - c.eps0_eV.lo) * (ze + 1.0) : c.eps0_eV.lo;
         t.Ex[q] = fr ? c.Ex_Vcm.lo + 0.5 * (c.Ex_Vcm.hi - c.Ex_Vcm.lo) * (zf + 1.0) : c.Ex_Vcm.lo;
         t.dq[q] = t.Ex[q] * 1.0e-7 * c.dt_fs / t.hbar_fs;
-        t.nq[q] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper(t.eps0[q], c.eps_F_eV, kT) * 1.0e18;
+        t.nq[q] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper<double>(t.eps0[q], c.eps_F_eV, kT) * 1.0e18;
         t.eps0_max = std::max(t.eps0_max, t.eps0[q]);
         basis_at(d, c.degree_M, d ? &t.z[(size_t)q * d] : nullptr, &t.psi[(size_t)q * P]);
         for (int h = 0; h < P; ++h) t.wpsi[(size_t)q * P + h] = t.w[q] * t.psi[(size_t)q * P + h];
@@ -237,16 +237,28 @@ struct FinArgs {
 };
 
 // fixed-order reduction of the block partials, node values, mean and variance (Sec. 4.2);
-// record = [t, nodes[Q][4] (Vx, Vy, E, Jx), mean[4], var[4]]
-__global__ void k_finalize(const double *part1, const double *part2, const __grid_constant__ FinArgs f, double *rec)
+// record = [t, nodes[Q][4] (Vx, Vy, E, Jx), mean[4], var[4]].  Thread t sums column t % n3 over
+// the blocks congruent to t / n3 (coalesced reads), then one thread per column adds the slots.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads)
+k_finalize(const double *part1, const double *part2, const __grid_constant__ FinArgs f, double *rec)
 {
+    __shared__ double red[kFinThreads];
     __shared__ double S[64 * 3];
     const int n3 = f.Q * 3;
-    for (int j = threadIdx.x; j < n3; j += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < f.g1; ++b) s += part1[(int64_t)b * n3 + j];
-        for (int b = 0; b < f.g2; ++b) s += part2[(int64_t)b * n3 + j];
-        S[j] = s;
+    const int nslot = kFinThreads / n3;
+    const int t = threadIdx.x, col = t % n3, slot = t / n3;
+    double s = 0.0;
+    if (slot < nslot) {
+        for (int b = slot; b < f.g1; b += nslot) s += part1[(int64_t)b * n3 + col];
+        for (int b = slot; b < f.g2; b += nslot) s += part2[(int64_t)b * n3 + col];
+    }
+    red[t] = s;
+    __syncthreads();
+    if (t < n3) {
+        double acc = 0.0;
+        for (int k = 0; k < nslot; ++k) acc += red[k * n3 + t];
+        S[t] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -492,7 +504,7 @@ static pgc_status observe_current(pgc_ctx *ctx, bool record, bool set_nmax)
         f.Q = ctx->t.Q;
         f.g1 = ctx->run->grid1();
         f.g2 = 0;
-        k_finalize<<<1, 128, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
+        k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
         count_launch();
         ctx->T_out++;
     }
@@ -606,7 +618,7 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
         ctx->step = n + 1;
         if (out) {
             f.t_fs = ctx->step * ctx->t.dt;
-            k_finalize<<<1, 128, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
+            k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
             count_launch();
             ctx->T_out++;
         }

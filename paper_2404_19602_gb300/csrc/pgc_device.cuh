@@ -146,7 +146,7 @@ __device__ __forceinline__ R rates6(const Phys<R> &ph, R kx, R ky, R eps0, R g[6
     } else {
         g[5] = (R)0;
     }
-    return ((g[0] + g[1]) + (g[2] + g[3])) + (g[4] + g[5]);
+    return ((((g[0] + g[1]) + g[2]) + g[3]) + g[4]) + g[5];  // the order of Eq. (20)
 }
 
 // Upper bound of sum_nu Gamma_nu over all states with energy <= eps and band minimum <= eps0max:
@@ -284,63 +284,85 @@ __device__ __forceinline__ bool pauli_accept(uint32_t H, uint32_t nmax, uint32_t
 // b = (e - mu)/kT.  Li2 for negative arguments: Bernoulli series in t = -ln(1 - x) on
 // [-1, 0], inversion formula below -1.
 // ------------------------------------------------------------------------------------------
-__host__ __device__ inline double li2_bern(double x)
+template <typename T>
+__host__ __device__ inline T li2_bern(T x)
 {
     // x in [-1, 0]:  Li2(x) = sum_n B_n t^{n+1}/(n+1)!,  t = -ln(1 - x),  |t| <= ln 2
-    const double t = -log1p(-x);
-    const double B[12] = {1.0 / 6.0, -1.0 / 30.0, 1.0 / 42.0, -1.0 / 30.0, 5.0 / 66.0,
-                          -691.0 / 2730.0, 7.0 / 6.0, -3617.0 / 510.0, 43867.0 / 798.0,
-                          -174611.0 / 330.0, 854513.0 / 138.0, -236364091.0 / 2730.0};
-    double s = t - 0.25 * t * t;  // B_0 t + B_1 t^2 / 2
-    double t2 = t * t, p = t * t2, fact = 6.0;  // t^3 / 3!
-    for (int k = 0; k < 12; ++k) {
+    const T t = -log1p(-x);
+    const T B[12] = {(T)(1.0 / 6.0), (T)(-1.0 / 30.0), (T)(1.0 / 42.0), (T)(-1.0 / 30.0), (T)(5.0 / 66.0),
+                     (T)(-691.0 / 2730.0), (T)(7.0 / 6.0), (T)(-3617.0 / 510.0), (T)(43867.0 / 798.0),
+                     (T)(-174611.0 / 330.0), (T)(854513.0 / 138.0), (T)(-236364091.0 / 2730.0)};
+    T s = t - (T)0.25 * t * t;  // B_0 t + B_1 t^2 / 2
+    T t2 = t * t, p = t * t2, fact = (T)6;  // t^3 / 3!
+    const int nterms = (sizeof(T) == 8) ? 12 : 5;
+    for (int k = 0; k < nterms; ++k) {
         s += B[k] * p / fact;
-        const double n = 2.0 * k + 3.0;  // next odd power
+        const T n = (T)(2 * k + 3);  // next odd power
         p *= t2;
-        fact *= (n + 1.0) * (n + 2.0);
+        fact *= (n + (T)1) * (n + (T)2);
     }
     return s;
 }
 
-__host__ __device__ inline double li2_negative(double x)
+template <typename T>
+__host__ __device__ inline T li2_negative(T x)
 {
-    if (x >= -1.0) return li2_bern(x);
-    const double l = log(-x);
-    return -kPi * kPi / 6.0 - 0.5 * l * l - li2_bern(1.0 / x);
+    if (x >= (T)-1) return li2_bern<T>(x);
+    const T l = log(-x);
+    return (T)(-kPi * kPi / 6.0) - (T)0.5 * l * l - li2_bern<T>((T)1 / x);
 }
 
-__host__ __device__ inline double fd_upper(double e, double mu, double kT)
+template <typename T>
+__host__ __device__ inline T fd_upper(T e, T mu, T kT)
 {
-    const double b = (e - mu) / kT;
-    const double l = (b > 0.0) ? log1p(exp(-b)) : -b + log1p(exp(b));
-    double li;
-    if (b > 700.0) li = 0.0;
-    else if (b < -700.0) li = -kPi * kPi / 6.0 - 0.5 * b * b;
-    else li = li2_negative(-exp(-b));
+    const T b = (e - mu) / kT;
+    const T l = (b > (T)0) ? log1p(exp(-b)) : -b + log1p(exp(b));
+    const T big = (sizeof(T) == 8) ? (T)700 : (T)80;
+    T li;
+    if (b > big) li = (T)0;
+    else if (b < -big) li = (T)(-kPi * kPi / 6.0) - (T)0.5 * b * b;
+    else li = li2_negative<T>(-exp(-b));
     return kT * (mu * l + kT * (b * l - li));
 }
 
-// eps with F(eps) = u for the density eps*FD on [eps0, inf): bisection, then Newton polish
+// eps with F(eps) = u for the density eps*FD on [eps0, inf): an FP32 bisection gives a bracket,
+// checked in FP64, then safeguarded Newton in FP64 (plain FP64 bisection if the check fails).
 __host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, double u)
 {
-    const double tot = fd_upper(eps0, mu, kT);
-    double lo = eps0, hi = fmax(mu, eps0) + 80.0 * kT;
+    const double tot = fd_upper<double>(eps0, mu, kT);
     auto resid = [&](double e) {  // F(e) - u  (upper-tail form for u >= 1/2)
-        return (u < 0.5) ? (tot - fd_upper(e, mu, kT)) / tot - u : (1.0 - u) - fd_upper(e, mu, kT) / tot;
+        return (u < 0.5) ? (tot - fd_upper<double>(e, mu, kT)) / tot - u : (1.0 - u) - fd_upper<double>(e, mu, kT) / tot;
     };
-    for (int it = 0; it < 40; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (resid(mid) < 0.0) lo = mid; else hi = mid;
+    const double top = fmax(mu, eps0) + 80.0 * kT;
+    double lo = eps0, hi = top;
+    {
+        const float e0f = (float)eps0, muf = (float)mu, kTf = (float)kT, uf = (float)u;
+        const float totf = fd_upper<float>(e0f, muf, kTf);
+        float lf = e0f, hf = (float)top;
+        for (int it = 0; it < 30; ++it) {
+            const float mid = 0.5f * (lf + hf);
+            if (!(mid > lf && mid < hf)) break;
+            const float rf = (uf < 0.5f) ? (totf - fd_upper<float>(mid, muf, kTf)) / totf - uf
+                                         : (1.0f - uf) - fd_upper<float>(mid, muf, kTf) / totf;
+            if (rf < 0.0f) lf = mid; else hf = mid;
+        }
+        const double w = 1e-4 * ((double)hf - (double)lf) + 1e-6 * (double)hf;
+        const double l2 = fmax(eps0, (double)lf - w), h2 = fmin(top, (double)hf + w);
+        if (resid(l2) <= 0.0 && resid(h2) >= 0.0) { lo = l2; hi = h2; }
     }
+    if (hi - lo > 1e-3 * hi)  // bracket check failed: FP64 bisection from the full range
+        for (int it = 0; it < 40; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (resid(mid) < 0.0) lo = mid; else hi = mid;
+        }
     double e = 0.5 * (lo + hi);
-    for (int it = 0; it < 12; ++it) {
+    for (int it = 0; it < 40; ++it) {
         const double r = resid(e);
-        const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
-        if (!(dens > 0.0)) break;
-        double en = e - r / dens;
-        if (en <= lo || en >= hi) en = 0.5 * (lo + hi);
         if (r < 0.0) lo = e; else hi = e;
-        if (fabs(en - e) <= 1e-16 * e) { e = en; break; }
+        const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
+        double en = (dens > 0.0) ? e - r / dens : 0.5 * (lo + hi);
+        if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
+        if (fabs(en - e) <= 2e-16 * e || hi - lo <= 4e-16 * hi) { e = en; break; }
         e = en;
     }
     return e;

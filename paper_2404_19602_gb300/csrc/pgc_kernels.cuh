@@ -23,6 +23,11 @@ constexpr int kPhase1Threads = 256;
 constexpr int kPhase2Threads = 128;
 constexpr int kMaxGrid1 = 4096;   // block partials sized for at most this many phase-1 blocks
 constexpr int kGrid2 = 608;       // phase-2 blocks (grid-stride over the queue)
+// Block-private histogram window of phase 1: kWin x kWin cells per node around the grid centre,
+// 16-bit counts packed two per 32-bit word in shared memory, flushed to the global histogram once
+// per block.  Cells outside the window go straight to the global histogram.
+constexpr int kWin = 32;
+constexpr int kWinWords = kWin * kWin / 2;
 
 // Quadrature / basis tables of one context (Sec. 4.1).
 template <int P, int Q, typename R>
@@ -55,6 +60,8 @@ struct StepArgs {
     unsigned long long *counters;
     uint32_t key0, key1, stream_id, step;
     int32_t out_step;        // 1: accumulate the moments of the post-step state
+    int32_t win_r0;          // first row / column of the shared-memory window
+    int32_t use_win;         // 1: phase 1 counts into the shared-memory window
 };
 
 template <typename T>
@@ -101,15 +108,53 @@ __device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, R
 }
 
 // ------------------------------------------------------------------------------------------
-// Phase 1: every particle.
+// Phase 1: every particle.  Each thread takes PPT consecutive particles and reads each
+// coefficient plane with one 16-byte load (float4 / 2 x double2); the ensemble is streamed once.
 // ------------------------------------------------------------------------------------------
+template <int P> struct Phase1PPT { static constexpr int value = (P <= 8) ? 4 : 1; };
+
+template <typename R, int PPT>
+__device__ __forceinline__ void load_vec(const R *p, R v[PPT])
+{
+    if constexpr (PPT == 4 && sizeof(R) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (PPT == 4 && sizeof(R) == 8) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int e = 0; e < PPT; ++e) v[e] = p[e];
+    }
+}
+
+template <typename R, int PPT>
+__device__ __forceinline__ void store_vec(R *p, const R v[PPT])
+{
+    if constexpr (PPT == 4 && sizeof(R) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (PPT == 4 && sizeof(R) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < PPT; ++e) p[e] = v[e];
+    }
+}
+
 template <int P, int Q, typename R>
 __global__ void __launch_bounds__(kPhase1Threads)
 k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
 {
+    constexpr int PPT = Phase1PPT<P>::value;
     constexpr int NW = kPhase1Threads / 32;
     __shared__ double smom[NW][Q * 3];
+    extern __shared__ uint32_t swin[];   // [Q][kWinWords] when a.use_win
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.use_win)
+        for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) swin[j] = 0u;
+    __syncthreads();
 
     // housekeeping for the next steps
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.qcount_next = 0u;
@@ -129,79 +174,119 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
     const Nodes<P, Q, R> &nd = a.nd;
     const int64_t NN = (int64_t)ph.Nk * ph.Nk;
     unsigned int oog = 0u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPT;
 
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < a.N;
-        R cx[P], cy[P];
-        bool finished = false;
-        if (valid) {
-            load_coeffs(a, i, cx, cy);
-            // drift (Eq. (17) / sG forcing term)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT; base < a.N; base += stride) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * PPT;
+        R cx[PPT][P], cy[PPT][P];
+        bool valid[PPT], finished[PPT];
+        const bool any = i0 < a.N;
+        if (any) {
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+                R vx[PPT], vy[PPT];
+                load_vec<R, PPT>(a.khat + (int64_t)h * a.ld + i0, vx);
+                load_vec<R, PPT>(a.khat + (int64_t)(P + h) * a.ld + i0, vy);
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) { cx[e][h] = vx[e]; cy[e][h] = vy[e]; }
+            }
+            // drift (Eq. (17) / sG forcing term); the padding beyond N is left untouched
 #pragma unroll
             for (int h = 0; h < P; ++h)
                 if (nd.drift_mask & (1u << h)) {
-                    cx[h] -= nd.dhat[h];
-                    a.khat[(int64_t)h * a.ld + i] = cx[h];
-                }
-            // reconstruction, cells and the bound on the majorant
-            int cell[Q];
-            R kkmax = (R)0;
+                    R v[PPT];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                R kx, ky;
-                recon_node(nd, q, cx, cy, kx, ky);
-                cell[q] = cell_of(ph, kx, ky);
-                kkmax = fmax(kkmax, kx * kx + ky * ky);
-            }
-            const U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, 0u, a.key0, a.key1);
-            const R lnxi = -rlog<R>(u01<R>(r.x));
-            const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
-            const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
-            const bool maybe = lnxi < gub * ph.dt;
-            if (!maybe) {
-                finished = true;
+                    for (int e = 0; e < PPT; ++e) {
+                        if (i0 + e < a.N) cx[e][h] -= nd.dhat[h];
+                        v[e] = cx[e][h];
+                    }
+                    store_vec<R, PPT>(a.khat + (int64_t)h * a.ld + i0, v);
+                }
+        }
+#pragma unroll
+        for (int e = 0; e < PPT; ++e) {
+            const int64_t i = i0 + e;
+            valid[e] = any && i < a.N;
+            finished[e] = false;
+            bool maybe = false;
+            if (valid[e]) {
+                // reconstruction, cells and the bound on the majorant
+                int cell[Q];
+                R kkmax = (R)0;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    if (cell[q] >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cell[q]], 1u);
-                    else ++oog;
+                    R kx, ky;
+                    recon_node(nd, q, cx[e], cy[e], kx, ky);
+                    cell[q] = cell_of(ph, kx, ky);
+                    kkmax = fmax(kkmax, kx * kx + ky * ky);
+                }
+                const U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, 0u, a.key0, a.key1);
+                const R lnxi = -rlog<R>(u01<R>(r.x));
+                const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
+                const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
+                maybe = lnxi < gub * ph.dt;
+                if (!maybe) {
+                    finished[e] = true;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const int cl = cell[q];
+                        if (cl < 0) { ++oog; continue; }
+                        const int rr = cl / ph.Nk - a.win_r0, ll = cl % ph.Nk - a.win_r0;
+                        if (a.use_win && (unsigned)rr < (unsigned)kWin && (unsigned)ll < (unsigned)kWin)
+                            atomicAdd(&swin[q * kWinWords + rr * (kWin / 2) + (ll >> 1)], 1u << ((ll & 1) << 4));
+                        else
+                            atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
+                    }
                 }
             }
             // colliders go to the queue (warp-aggregated append)
-            const unsigned int mask = __ballot_sync(__activemask(), maybe);
-            if (maybe) {
+            const unsigned int mask = __ballot_sync(0xffffffffu, maybe);
+            if (mask) {
                 const int leader = __ffs(mask) - 1;
                 uint32_t basepos = 0;
                 if (lane == leader) basepos = atomicAdd(a.qcount, (uint32_t)__popc(mask));
-                basepos = __shfl_sync(mask, basepos, leader);
-                const uint32_t off = __popc(mask & ((1u << lane) - 1u));
-                a.queue[basepos + off] = (uint32_t)i;
+                basepos = __shfl_sync(0xffffffffu, basepos, leader);
+                if (maybe) a.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)i;
             }
         }
         if (a.out_step) {
 #pragma unroll 1
             for (int q = 0; q < Q; ++q) {
-                R vx = (R)0, vy = (R)0, e = (R)0;
-                if (finished) {
-                    R kx, ky;
-                    recon_node(nd, q, cx, cy, kx, ky);
-                    observe(ph, kx, ky, nd.eps0[q], vx, vy, e);
-                }
+                R vx = (R)0, vy = (R)0, en = (R)0;
+#pragma unroll
+                for (int e = 0; e < PPT; ++e)
+                    if (finished[e]) {
+                        R kx, ky, a1, a2, a3;
+                        recon_node(nd, q, cx[e], cy[e], kx, ky);
+                        observe(ph, kx, ky, nd.eps0[q], a1, a2, a3);
+                        vx += a1; vy += a2; en += a3;
+                    }
                 vx = warp_sum(vx);
                 vy = warp_sum(vy);
-                e = warp_sum(e);
+                en = warp_sum(en);
                 if (lane == 0) {
                     smom[warp][q * 3 + 0] += (double)vx;
                     smom[warp][q * 3 + 1] += (double)vy;
-                    smom[warp][q * 3 + 2] += (double)e;
+                    smom[warp][q * 3 + 2] += (double)en;
                 }
             }
         }
     }
     oog = warp_sum(oog);
     if (lane == 0 && oog) atomicAdd(&a.counters[4], (unsigned long long)oog);
+    __syncthreads();
+    if (a.use_win) {  // flush the block's window: one global add per non-empty cell
+        for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) {
+            const uint32_t v = swin[j];
+            if (!v) continue;
+            const int q = j / kWinWords, w = j % kWinWords;
+            const int rr = w / (kWin / 2) + a.win_r0, ll = 2 * (w % (kWin / 2)) + a.win_r0;
+            uint32_t *base = a.Hnext + (int64_t)q * NN + (int64_t)rr * ph.Nk + ll;
+            if (v & 0xffffu) atomicAdd(base, v & 0xffffu);
+            if (v >> 16) atomicAdd(base + 1, v >> 16);
+        }
+    }
     if (a.out_step) {
-        __syncthreads();
         for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
             double s = 0.0;
 #pragma unroll
@@ -212,25 +297,44 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
 }
 
 // ------------------------------------------------------------------------------------------
-// Phase 2: the collision loop of Algorithm 1 / 2 for the queued particles.
+// Phase 2: the collision loop of Algorithm 1 / 2 for the queued particles.  A group of G
+// lanes carries one particle, lane r owning the nodes q = r, r + G, ... (lanes <-> quadrature
+// nodes): the rates, the mechanism selection, the final states and the Pauli look-ups of the Q
+// nodes run in parallel, and the projection of Eqs. (28)-(30) and the majorant of Eq. (25) are
+// group reductions by shuffles.
 // ------------------------------------------------------------------------------------------
-template <int P, int Q, typename R>
-__device__ __forceinline__ R majorant(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const R *kx, const R *ky)
+template <int Q> struct GroupOf {
+    static constexpr int G = (Q >= 32) ? 32 : (Q > 16 ? 32 : (Q > 8 ? 16 : (Q > 4 ? 8 : (Q > 2 ? 4 : (Q > 1 ? 2 : 1)))));
+    static constexpr int NPL = (Q + G - 1) / G;  // nodes per lane
+};
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask)
 {
-    R gmax = (R)0;
-#pragma unroll 1
-    for (int q = 0; q < Q; ++q) {
-        R g[6];
-        const R s = rates6(ph, kx[q], ky[q], nd.eps0[q], g);
-        gmax = fmax(gmax, s);
-    }
-    return ph.alpha1 * gmax;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_max(T v, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool b, unsigned mask)
+{
+    return (__ballot_sync(mask, b) & mask) != 0u;
 }
 
 template <int P, int Q, typename R>
 __global__ void __launch_bounds__(kPhase2Threads)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
+    constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
     __shared__ double smom[Q * 3];
     __shared__ unsigned long long scnt[5];
     if (threadIdx.x < 5) scnt[threadIdx.x] = 0ull;
@@ -243,30 +347,53 @@ k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
     const uint32_t count = *a.qcount;
     unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0;
 
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int r = lane % G;                                  // lane in the group
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
+    const uint32_t gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const uint32_t ngroups = gridDim.x * blockDim.x / G;
+
+    for (uint32_t j = gid; j < count; j += ngroups) {
         const int64_t i = a.queue[j];
-        R cx[P], cy[P], kx[Q], ky[Q];
+        R cx[P], cy[P], kx[NPL], ky[NPL];
         load_coeffs(a, i, cx, cy);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) recon_node(nd, q, cx, cy, kx[q], ky[q]);
-        R Gt = majorant(ph, nd, kx, ky);
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+        }
+        auto majorant = [&]() {
+            R gm = (R)0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) {
+                    R g[6];
+                    gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], g));
+                }
+            }
+            return ph.alpha1 * group_max<G>(gm, gmask);
+        };
+        R Gt = majorant();
         R tc = (R)0;
         uint32_t c = 0;
-        U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
-        R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(r.x)) / Gt : (R)INFINITY;
+        U4 rr = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
+        R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
         bool touched = false;
-        while (tc + dtc < ph.dt) {
-            if ((int)c >= ph.max_coll) { ++cap; break; }
-            ++att;
+        while (tc + dtc < ph.dt) {               // group-uniform condition
+            if ((int)c >= ph.max_coll) { if (r == 0) ++cap; break; }
+            if (r == 0) ++att;
             touched = true;
             EventAngles<R> ang;
-            ang.reset(u01<R>(r.w));
-            const R target = u01<R>(r.y) * Gt;
+            ang.reset(u01<R>(rr.w));
+            const R target = u01<R>(rr.y) * Gt;
             bool changed = false;
-#pragma unroll 1
-            for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q >= Q) continue;
                 R g[6];
-                rates6(ph, kx[q], ky[q], nd.eps0[q], g);
+                rates6(ph, kx[s], ky[s], nd.eps0[q], g);
                 int l = 6;
                 R cum = (R)0;
 #pragma unroll
@@ -276,51 +403,62 @@ k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
                 }
                 if (l == 6) continue;  // self scattering: h^7 = identity
                 R nkx, nky;
-                final_state(ph, l, kx[q], ky[q], nd.eps0[q], ang, &nkx, &nky);
+                final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
                 bool accept = true;
                 if (ph.pauli_mode != 2) {
                     const int cl = cell_of(ph, nkx + nd.dq[q], nky);
-                    if (cl >= 0) accept = pauli_accept(a.Hcur[(int64_t)q * NN + cl], a.nmax[q], r.z);
+                    if (cl >= 0) accept = pauli_accept(a.Hcur[(int64_t)q * NN + cl], a.nmax[q], rr.z);
                 }
-                if (accept) { kx[q] = nkx; ky[q] = nky; changed = true; }
+                if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
                 else ++rej;
             }
-            if (changed) ++chg;
+            if (group_any<G>(changed, gmask) && r == 0) ++chg;
             // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
 #pragma unroll
             for (int h = 0; h < P; ++h) {
                 R sx = (R)0, sy = (R)0;
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    sx += nd.wpsi[q * P + h] * kx[q];
-                    sy += nd.wpsi[q * P + h] * ky[q];
+                for (int s = 0; s < NPL; ++s) {
+                    const int q = r + s * G;
+                    if (q < Q) {
+                        sx += nd.wpsi[q * P + h] * kx[s];
+                        sy += nd.wpsi[q * P + h] * ky[s];
+                    }
                 }
-                cx[h] = sx;
-                cy[h] = sy;
+                cx[h] = group_sum<G>(sx, gmask);
+                cy[h] = group_sum<G>(sy, gmask);
             }
 #pragma unroll
-            for (int q = 0; q < Q; ++q) recon_node(nd, q, cx, cy, kx[q], ky[q]);
-            Gt = majorant(ph, nd, kx, ky);
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+            }
+            Gt = majorant();
             tc += dtc;
             ++c;
-            r = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
-            dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(r.x)) / Gt : (R)INFINITY;
+            rr = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
+            dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
         }
         if (touched) {
+            // lane h of the group writes coefficient h (x and y planes)
+            for (int h = r; h < P; h += G) {
+                R vx = cx[0], vy = cy[0];
 #pragma unroll
-            for (int h = 0; h < P; ++h) {
-                a.khat[(int64_t)h * a.ld + i] = cx[h];
-                a.khat[(int64_t)(P + h) * a.ld + i] = cy[h];
+                for (int hh = 0; hh < P; ++hh) if (hh == h) { vx = cx[hh]; vy = cy[hh]; }
+                a.khat[(int64_t)h * a.ld + i] = vx;
+                a.khat[(int64_t)(P + h) * a.ld + i] = vy;
             }
         }
-#pragma unroll 1
-        for (int q = 0; q < Q; ++q) {
-            const int cl = cell_of(ph, kx[q], ky[q]);
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q >= Q) continue;
+            const int cl = cell_of(ph, kx[s], ky[s]);
             if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
             else ++oog;
             if (a.out_step) {
                 R vx, vy, e;
-                observe(ph, kx[q], ky[q], nd.eps0[q], vx, vy, e);
+                observe(ph, kx[s], ky[s], nd.eps0[q], vx, vy, e);
                 atomicAdd(&smom[q * 3 + 0], (double)vx);
                 atomicAdd(&smom[q * 3 + 1], (double)vy);
                 atomicAdd(&smom[q * 3 + 2], (double)e);

@@ -40,12 +40,26 @@ public:
         init_.mu = t.mu;
         init_.kT = t.kT;
         init_.hvF = t.hvF;
-        // phase-1 grid: enough resident blocks to fill the GPU, at most one particle per thread
+        // phase-1 grid: enough resident blocks to fill the GPU, PPT particles per thread; the
+        // shared-memory histogram window needs every cell of a window to receive < 2^16 counts
+        // from one block, and a window that lies inside the grid
+        constexpr int PPT = Phase1PPT<P>::value;
+        win_bytes_ = (size_t)Q * kWinWords * 4;
+        args_.win_r0 = std::max(0, t.Nk / 2 - kWin / 2);
+        bool win = t.Nk >= kWin && win_bytes_ <= 160 * 1024;
+        if (win && cudaFuncSetAttribute(k_phase1<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_) != cudaSuccess) {
+            cudaGetLastError();
+            win = false;
+        }
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase1<P, Q, R>, kPhase1Threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase1<P, Q, R>, kPhase1Threads, win ? win_bytes_ : 0);
         per_sm = std::max(per_sm, 1);
-        const int64_t need = (b.N + kPhase1Threads - 1) / kPhase1Threads;
+        const int64_t need = (b.N + (int64_t)kPhase1Threads * PPT - 1) / ((int64_t)kPhase1Threads * PPT);
         grid1_ = (int)std::max<int64_t>(1, std::min<int64_t>({need, (int64_t)num_sms * per_sm, (int64_t)kMaxGrid1}));
+        const int64_t per_block = (b.N + grid1_ - 1) / grid1_;
+        if (per_block >= 65535) win = false;
+        args_.use_win = win ? 1 : 0;
+        if (!win) win_bytes_ = 0;
     }
 
     int grid1() const override { return grid1_; }
@@ -80,7 +94,7 @@ public:
         a.step = (uint32_t)step;
         a.out_step = out_step ? 1 : 0;
         if (ev) cudaEventRecord(ev[0], s);
-        k_phase1<P, Q, R><<<grid1_, kPhase1Threads, 0, s>>>(a);
+        k_phase1<P, Q, R><<<grid1_, kPhase1Threads, win_bytes_, s>>>(a);
         if (ev) cudaEventRecord(ev[1], s);
         k_phase2<P, Q, R><<<kGrid2, kPhase2Threads, 0, s>>>(a);
         if (ev) cudaEventRecord(ev[2], s);
@@ -138,6 +152,7 @@ private:
     StepArgs<P, Q, R> args_{};
     InitArgs<P, Q> init_{};
     int grid1_ = 1;
+    size_t win_bytes_ = 0;
 };
 
 template <int P, int Q>
