@@ -187,6 +187,21 @@ void pgc_destroy(pgc_ctx *ctx);
 const char *pgc_last_error(const pgc_ctx *ctx);
 const char *pgc_status_string(pgc_status s);
 
+/* Observation of the current state that allocates nothing (the paper has no counterpart; this
+ * is a service for callers that may not allocate device memory while they run, e.g. because a
+ * framework's pool owns all device memory, or because cudaMalloc / cudaFree could synchronize the
+ * device under queued work).  Writes the histogram of the current state at the quadrature nodes
+ * to d_hist_out (device, uint32 [Q][Nk][Nk], cleared by the call) and one moment record to
+ * d_record_out (device, double [1 + 4Q + 8]: t_fs, nodes[Q][4], mean[4], var[4], the layout of
+ * pgc_moments).  Its block-partial scratch is a fixed 4 MiB device array inside the library
+ * (held by every GPU that loads the library until exit): configurations whose partial sums need
+ * more are rejected with PGC_EINVAL and a message.  No cudaMalloc/cudaFree or other allocating
+ * call is made.  The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (unordered streams) race.  Runs on
+ * `stream`, which must be ordered after the context's pending work. */
+pgc_status pgc_observe_static(pgc_ctx *ctx, uint32_t *d_hist_out, double *d_record_out, void *stream);
+
 /* Number of kernel launches issued by the library since load (for launch accounting). */
 uint64_t pgc_launch_count(void);
 

@@ -17,6 +17,7 @@
 #include "pgc_device.cuh"
 #include "pgc_kernels.cuh"
 #include "pgc_runner.h"
+#include "pgc_ctx.h"
 
 namespace pgc {
 
@@ -301,33 +302,27 @@ __global__ void k_hist_max(const uint32_t *H, int64_t cells, uint32_t *out)
     }
 }
 
+// Fixed-order reduction of g1 block partials (no second set) into one moment record of ctx's
+// layout; used by entry points that keep their partial sums outside the context scratch.
+cudaError_t launch_finalize(const pgc_ctx *ctx, const double *part, int g1, double t_fs, double *rec,
+                            cudaStream_t s)
+{
+    FinArgs f{};
+    for (int q = 0; q < ctx->t.Q; ++q) { f.nq[q] = ctx->t.nq[q]; f.w[q] = ctx->t.w[q]; }
+    f.N = (double)ctx->b.N;
+    f.vF_ms = ctx->t.vF_ms;
+    f.t_fs = t_fs;
+    f.Q = ctx->t.Q;
+    f.g1 = g1;
+    f.g2 = 0;
+    k_finalize<<<1, kFinThreads, 0, s>>>(part, nullptr, f, rec);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace pgc
 
 using namespace pgc;
-
-struct pgc_ctx {
-    pgc_config cfg{};
-    HostTables t;
-    DevBuffers b;
-    Runner *run = nullptr;
-    cudaStream_t stream = nullptr;
-    int64_t step = 0;
-    int64_t T_out = 0;
-    int rec_len = 0;
-    double *series = nullptr;
-    uint32_t *tmp_max = nullptr;
-    bool failed = false;
-    std::string err;
-    // kernel timing samples (pgc_profile): events around phase 1 / phase 2 of sampled steps
-    int prof_every = 0;
-    std::vector<cudaEvent_t> prof_ev;  // 3 per sample
-    int prof_used = 0;
-    double prof_ms[2] = {0.0, 0.0};
-    int64_t prof_samples = 0;
-    // pinned host staging buffer of the state transfers (allocated on first use)
-    void *pinned = nullptr;
-    size_t pinned_bytes = 0;
-};
 
 static void *staging(pgc_ctx *ctx, size_t bytes)
 {

@@ -1,0 +1,40 @@
+// pgc_ctx.h -- the context behind the opaque pgc_ctx handle of include/pgc.h.  Internal.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pgc.h"
+#include "pgc_runner.h"
+
+struct pgc_ctx {
+    pgc_config cfg{};
+    pgc::HostTables t;
+    pgc::DevBuffers b;
+    pgc::Runner *run = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t step = 0;
+    int64_t T_out = 0;
+    int rec_len = 0;
+    double *series = nullptr;
+    uint32_t *tmp_max = nullptr;
+    bool failed = false;
+    std::string err;
+    // kernel timing samples (pgc_profile): events around phase 1 / phase 2 of sampled steps
+    int prof_every = 0;
+    std::vector<cudaEvent_t> prof_ev;  // 3 per sample
+    int prof_used = 0;
+    double prof_ms[2] = {0.0, 0.0};
+    int64_t prof_samples = 0;
+    // pinned host staging buffer of the state transfers (allocated on first use)
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+};
+
+
+namespace pgc {
+cudaError_t launch_finalize(const pgc_ctx *ctx, const double *part, int g1, double t_fs, double *rec,
+                            cudaStream_t s);
+}  // namespace pgc

@@ -55,6 +55,9 @@ public:
     virtual cudaError_t init_sample(cudaStream_t s) = 0;
     // histogram of the current state into hist buffer `buf` and moment partials into part1
     virtual cudaError_t observe(int buf, cudaStream_t s) = 0;
+    // histogram of the current state into `hist` ([Q][Nk*Nk], zeroed by the caller) and moment
+    // partials into `part` ([grid1()][Q*3]); touches no context buffer
+    virtual cudaError_t observe_into(uint32_t *hist, double *part, cudaStream_t s) = 0;
     // time step number `step` (histograms rotate over the three buffers); if ev is non-NULL,
     // ev[0..2] are recorded before phase 1, between the phases and after phase 2
     virtual cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev = nullptr) = 0;

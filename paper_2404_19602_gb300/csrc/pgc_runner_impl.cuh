@@ -82,6 +82,17 @@ public:
         return cudaGetLastError();
     }
 
+    cudaError_t observe_into(uint32_t *hist, double *part, cudaStream_t s) override
+    {
+        StepArgs<P, Q, R> a = args_;
+        a.Hnext = hist;
+        a.part1 = part;
+        a.out_step = 1;
+        k_observe<P, Q, R><<<grid1_, kPhase1Threads, 0, s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
     cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev) override
     {
         StepArgs<P, Q, R> a = args_;

@@ -70,6 +70,7 @@ SIGNATURES = {
     "pgc_get_hist": (C.c_int, [_vp, _u32p, _u32p]),
     "pgc_profile": (C.c_int, [_vp, C.c_int32]),
     "pgc_profile_read": (C.c_int, [_vp, _dp, _dp, _i64p]),
+    "pgc_observe_static": (C.c_int, [_vp, _vp, _vp, _vp]),
     "pgc_destroy": (None, [_vp]),
     "pgc_last_error": (C.c_char_p, [_vp]),
     "pgc_status_string": (C.c_char_p, [C.c_int]),
@@ -186,6 +187,12 @@ def pgc_profile_read(ctx):
     a, b, n = C.c_double(), C.c_double(), C.c_int64()
     _check(lib().pgc_profile_read(_vp(ctx), C.byref(a), C.byref(b), C.byref(n)), _vp(ctx))
     return dict(phase1_ms=a.value, phase2_ms=b.value, samples=n.value)
+
+
+def pgc_observe_static(ctx, d_hist_out: int, d_record_out: int, stream: int = 0):
+    """No-allocation observation: histogram of the current state and one moment record, both
+    written to caller-owned device buffers (see include/pgc.h)."""
+    _check(lib().pgc_observe_static(_vp(ctx), _vp(d_hist_out), _vp(d_record_out), _vp(stream)), _vp(ctx))
 
 
 def pgc_destroy(ctx):
