@@ -11,6 +11,7 @@
 namespace pgc {
 
 constexpr int kMaxTheta = 256;   // upper bound of the edge trapezoid points
+constexpr int kSerMax = 17;      // maximum order + 1 of the edge-integral series
 constexpr double kPi = 3.14159265358979323846;
 
 // ------------------------------------------------------------------------------------------
@@ -33,6 +34,10 @@ struct Phys {
     R bound_edge;         // 2 pi * (1 + 1e-5): upper bound of the trapezoid T
     R vF_ms;              // vF in m/s
     R cosj[kMaxTheta + 1];// cos(2 pi j / n_theta), j = 0..n_theta
+    // power series of T in beta (see edge_T): coefficient (j, m) of beta^j (c^2)^(j-m)
+    R tser[kSerMax * kSerMax];
+    R beta_ser;           // the series is used for beta <= beta_ser
+    int32_t J;            // series order
     uint32_t mech;
     int32_t n_theta;
     int32_t pauli_mode;   // 0 initial max, 1 current max, 2 off
@@ -94,6 +99,24 @@ template <> __device__ __forceinline__ double rfloor<double>(double x) { return 
 // divides (as the definition reads); the FP32 mode multiplies by the reciprocal.
 // ------------------------------------------------------------------------------------------
 template <typename R>
+__device__ __forceinline__ bool cell_rl(const Phys<R> &ph, R kx, R ky, int &r, int &l)
+{
+    R fr, fl;
+    if constexpr (sizeof(R) == 8) {
+        fr = floor((kx + ph.Lk) / ph.dk);
+        fl = floor((ky + ph.Lk) / ph.dk);
+    } else {
+        fr = floorf((kx + ph.Lk) * ph.inv_dk);
+        fl = floorf((ky + ph.Lk) * ph.inv_dk);
+    }
+    const R nk = (R)ph.Nk;
+    if (!(fr >= (R)0) || !(fl >= (R)0) || fr >= nk || fl >= nk) return false;
+    r = (int)fr;
+    l = (int)fl;
+    return true;
+}
+
+template <typename R>
 __device__ __forceinline__ int cell_of(const Phys<R> &ph, R kx, R ky)
 {
     R fr, fl;
@@ -110,12 +133,33 @@ __device__ __forceinline__ int cell_of(const Phys<R> &ph, R kx, R ky)
 }
 
 // ------------------------------------------------------------------------------------------
-// Edge integral T(|k|, c) = int_0^{2pi} exp(-beta (cos th' - c)^2) d th' by the trapezoid rule
-// on n_theta points (Appendix A), using the mirror symmetry th' -> 2pi - th'.
+// Edge integral T(|k|, c) = int_0^{2pi} exp(-beta (cos th' - c)^2) d th' (Appendix A).
+// The paper evaluates it by the trapezoid rule.  For a periodic analytic integrand the
+// n_theta-point rule is exact up to the Fourier modes of order >= n_theta, whose weight is
+// ~beta^(n_theta/2)/(n_theta/2)!: for beta <= beta_ser the rule equals the integral to working
+// precision, and the integral is summed from its power series
+//   T/(2 pi) = sum_j (-beta)^j / j! E[(cos th' - c)^{2j}],
+//   E[(cos th' - c)^{2j}] = sum_m C(2j,2m) C(2m,m) 4^-m c^{2(j-m)}
+// (J + 1 terms, Horner in c^2 and beta).  Otherwise: the trapezoid rule itself, using the
+// mirror symmetry th' -> 2pi - th'.
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R edge_T(const Phys<R> &ph, R beta, R c)
 {
+    if (beta <= ph.beta_ser) {
+        constexpr int J = (sizeof(R) == 8) ? 16 : 10;
+        const R x = c * c;
+        R acc = (R)0;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const R *a = &ph.tser[j * kSerMax];
+            R p = a[0];
+#pragma unroll
+            for (int m = 1; m <= j; ++m) p = p * x + a[m];
+            acc = acc * beta + p;
+        }
+        return (R)(2.0 * kPi) * acc;
+    }
     const int half = ph.n_theta >> 1;
     R x0 = ph.cosj[0] - c, xh = ph.cosj[half] - c;
     R s = rexp<R>(-beta * x0 * x0) + rexp<R>(-beta * xh * xh);

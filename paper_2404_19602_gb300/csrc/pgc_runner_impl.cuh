@@ -22,6 +22,14 @@ public:
         for (int h = 0; h < P; ++h) nd.dhat[h] = (R)t.dhat[h];
         for (int q = 0; q < Q; ++q) { nd.eps0[q] = (R)t.eps0[q]; nd.dq[q] = (R)t.dq[q]; }
         nd.eps0_max = (R)t.eps0_max;
+        if constexpr (TensorShape<P, Q>::value) {
+            // psi(q1,q2) = a_h1(z1_q1) b_h2(z2_q2) with a_0 = b_0 = 1
+            for (int q = 0; q < 6; ++q)
+                for (int h = 0; h < 6; ++h) {
+                    nd.a1[q * 6 + h] = (R)t.psi[(size_t)(q * 6) * P + hidx2(h, 0)];
+                    nd.b2[q * 6 + h] = (R)t.psi[(size_t)q * P + hidx2(0, h)];
+                }
+        }
         nd.drift_mask = t.drift_mask;
         args_.khat = static_cast<R *>(b.state);
         args_.N = b.N;
@@ -150,6 +158,16 @@ private:
         p.vF_ms = (R)t.vF_ms;
         const double h = 2.0 * kPi / t.n_theta;
         for (int j = 0; j <= kMaxTheta; ++j) p.cosj[j] = (R)((j <= t.n_theta) ? std::cos(j * h) : 1.0);
+        // edge-integral series: a[j][m] = (-1)^j / j! C(2j,2m) C(2m,m) 4^-m
+        p.J = (sizeof(R) == 8) ? 16 : 10;
+        p.beta_ser = (R)((t.n_theta >= 32) ? 0.25 : 0.0);
+        auto binom = [](int n, int k) { double r = 1.0; for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i; return r; };
+        for (int j = 0; j < kSerMax; ++j) {
+            double fact = 1.0;
+            for (int i = 2; i <= j; ++i) fact *= i;
+            for (int m = 0; m < kSerMax; ++m)
+                p.tser[j * kSerMax + m] = (R)((m <= j) ? ((j & 1) ? -1.0 : 1.0) / fact * binom(2 * j, 2 * m) * binom(2 * m, m) / std::pow(4.0, m) : 0.0);
+        }
         p.mech = t.mech;
         p.n_theta = t.n_theta;
         p.pauli_mode = t.pauli_mode;
