@@ -202,6 +202,41 @@ const char *pgc_status_string(pgc_status s);
  * `stream`, which must be ordered after the context's pending work. */
 pgc_status pgc_observe_static(pgc_ctx *ctx, uint32_t *d_hist_out, double *d_record_out, void *stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Batched sweep: many contexts ("cases" with different fields, band-minimum intervals and    */
+/* particle counts, the same basis, precision and physics) advanced together.  Each time step */
+/* is one persistent phase-1 launch over a tile list of all cases, one collider launch and one */
+/* finalize launch; the step index lives in device memory, so the sequence is captured once   */
+/* into a CUDA graph and replayed.  Every case follows exactly the trajectory its context      */
+/* would follow alone (same Philox streams, same arithmetic; only the grouping of the FP64      */
+/* moment partial sums differs).  The contexts keep their buffers and moment series; after     */
+/* pgc_batch_step their step counters and series have advanced as by pgc_step.                */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct pgc_batch pgc_batch;
+
+/* Check that the contexts can be batched (same shape, precision and physics, same step and
+ * stream, Pauli mode initial-max or off, < 2^32 particles in total) and report the bytes of the
+ * caller-owned device scratch the batch needs (case table, collider queue, partial sums). */
+pgc_status pgc_batch_query_sizes(pgc_ctx *const *ctxs, int32_t n_cases, size_t *scratch_bytes);
+
+/* Create a batch over ctxs[0..n_cases) (the contexts must outlive it) with caller scratch of the
+ * queried size (256-byte aligned).  tile_particles: particles per tile of the phase-1 work list
+ * (a multiple of the block pass, 1024 for P <= 8 and 256 otherwise; 0 = 8 passes). */
+pgc_status pgc_batch_create(pgc_ctx *const *ctxs, int32_t n_cases, void *d_scratch, int32_t tile_particles,
+                            pgc_batch **out);
+
+/* Advance every case by n_steps; moments as in pgc_step.  use_graph != 0 replays a captured
+ * graph of 10 time steps (the stream must not be the legacy default stream). */
+pgc_status pgc_batch_step(pgc_batch *b, int64_t n_steps, int32_t moments_every, int32_t use_graph);
+
+/* Autotuner: time steps_per_candidate time steps (no moments) for every tile size from one pass
+ * to 32768 particles, keep the fastest; *chosen_tile and *ms_per_step (either may be NULL)
+ * report it.  The timed steps advance the simulation (tile sizes do not change trajectories). */
+pgc_status pgc_batch_autotune(pgc_batch *b, int32_t steps_per_candidate, int32_t *chosen_tile, double *ms_per_step);
+
+void pgc_batch_destroy(pgc_batch *b);
+const char *pgc_batch_last_error(const pgc_batch *b);
+
 /* Number of kernel launches issued by the library since load (for launch accounting). */
 uint64_t pgc_launch_count(void);
 

@@ -193,6 +193,136 @@ __device__ __forceinline__ void store_vec(R *p, const R v[PPT])
     }
 }
 
+// Everything phase 1 needs about one ensemble (one case of a batch).
+template <typename R>
+struct P1Target {
+    R *khat;
+    int64_t N, ld;
+    uint32_t *Hnext;          // f^{n+1} [Q][Nk*Nk]
+    uint32_t *qcount;         // collider counter of this step
+    uint32_t *queue;          // collider queue
+    uint32_t qoffset;         // added to the particle index in queue entries
+    uint32_t key0, key1, stream_id, step;
+};
+
+// One pass of a block over blockDim * PPT consecutive particles starting at i0 + threadIdx*PPT:
+// drift, reconstruction, flight-time screen, histogram (window or global), queue, moments.
+template <int P, int Q, typename R>
+__device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const P1Target<R> &t,
+                                            int64_t i0, uint32_t *swin, int win_r0, bool use_win, bool out_step,
+                                            double *smom_warp, unsigned int &oog)
+{
+    constexpr int PPT = Phase1PPT<P>::value;
+    const int lane = threadIdx.x & 31;
+    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    R cx[PPT][P], cy[PPT][P];
+    bool finished[PPT];
+    const bool any = i0 < t.N;
+    if (any) {
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            R vx[PPT], vy[PPT];
+            load_vec<R, PPT>(t.khat + (int64_t)h * t.ld + i0, vx);
+            load_vec<R, PPT>(t.khat + (int64_t)(P + h) * t.ld + i0, vy);
+#pragma unroll
+            for (int e = 0; e < PPT; ++e) { cx[e][h] = vx[e]; cy[e][h] = vy[e]; }
+        }
+        // drift (Eq. (17) / sG forcing term); the padding beyond N is left untouched
+#pragma unroll
+        for (int h = 0; h < P; ++h)
+            if (nd.drift_mask & (1u << h)) {
+                R v[PPT];
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    if (i0 + e < t.N) cx[e][h] -= nd.dhat[h];
+                    v[e] = cx[e][h];
+                }
+                store_vec<R, PPT>(t.khat + (int64_t)h * t.ld + i0, v);
+            }
+    }
+#pragma unroll
+    for (int e = 0; e < PPT; ++e) {
+        const int64_t i = i0 + e;
+        finished[e] = false;
+        bool maybe = false;
+        if (any && i < t.N) {
+            // reconstruction, cells and the bound on the majorant
+            int rl[Q];   // cell (row << 16) | column; -1 outside the grid
+            R kkmax = (R)0;
+            recon_all(nd, cx[e], cy[e], [&](int q, R kx, R ky) {
+                int r, l;
+                rl[q] = cell_rl(ph, kx, ky, r, l) ? ((r << 16) | l) : -1;
+                kkmax = fmax(kkmax, kx * kx + ky * ky);
+            });
+            const U4 r = philox4x32_10((uint32_t)i, t.stream_id, t.step, 0u, t.key0, t.key1);
+            const R lnxi = -rlog<R>(u01<R>(r.x));
+            const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
+            const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
+            maybe = lnxi < gub * ph.dt;
+            if (!maybe) {
+                finished[e] = true;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    if (rl[q] < 0) { ++oog; continue; }
+                    const int r = rl[q] >> 16, l = rl[q] & 0xffff;
+                    const int rr = r - win_r0, ll = l - win_r0;
+                    if (use_win && (unsigned)rr < (unsigned)kWin && (unsigned)ll < (unsigned)kWin)
+                        atomicAdd(&swin[q * kWinWords + rr * (kWin / 2) + (ll >> 1)], 1u << ((ll & 1) << 4));
+                    else
+                        atomicAdd(&t.Hnext[(int64_t)q * NN + r * ph.Nk + l], 1u);
+                }
+            }
+        }
+        // colliders go to the queue (warp-aggregated append)
+        const unsigned int mask = __ballot_sync(0xffffffffu, maybe);
+        if (mask) {
+            const int leader = __ffs(mask) - 1;
+            uint32_t basepos = 0;
+            if (lane == leader) basepos = atomicAdd(t.qcount, (uint32_t)__popc(mask));
+            basepos = __shfl_sync(0xffffffffu, basepos, leader);
+            if (maybe) t.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = t.qoffset + (uint32_t)i;
+        }
+    }
+    if (out_step) {
+#pragma unroll 1
+        for (int q = 0; q < Q; ++q) {
+            R vx = (R)0, vy = (R)0, en = (R)0;
+#pragma unroll
+            for (int e = 0; e < PPT; ++e)
+                if (finished[e]) {
+                    R kx, ky, a1, a2, a3;
+                    recon_node(nd, q, cx[e], cy[e], kx, ky);
+                    observe(ph, kx, ky, nd.eps0[q], a1, a2, a3);
+                    vx += a1; vy += a2; en += a3;
+                }
+            vx = warp_sum(vx);
+            vy = warp_sum(vy);
+            en = warp_sum(en);
+            if (lane == 0) {
+                smom_warp[q * 3 + 0] += (double)vx;
+                smom_warp[q * 3 + 1] += (double)vy;
+                smom_warp[q * 3 + 2] += (double)en;
+            }
+        }
+    }
+}
+
+// Add a block's shared-memory window to the global histogram: one add per non-empty cell.
+template <int Q>
+__device__ __forceinline__ void flush_window(const uint32_t *swin, uint32_t *Hnext, int Nk, int win_r0)
+{
+    const int64_t NN = (int64_t)Nk * Nk;
+    for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) {
+        const uint32_t v = swin[j];
+        if (!v) continue;
+        const int q = j / kWinWords, w = j % kWinWords;
+        const int rr = w / (kWin / 2) + win_r0, ll = 2 * (w % (kWin / 2)) + win_r0;
+        uint32_t *base = Hnext + (int64_t)q * NN + (int64_t)rr * Nk + ll;
+        if (v & 0xffffu) atomicAdd(base, v & 0xffffu);
+        if (v >> 16) atomicAdd(base + 1, v >> 16);
+    }
+}
+
 template <int P, int Q, typename R>
 __global__ void __launch_bounds__(kPhase1Threads)
 k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
@@ -220,120 +350,18 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
     if (a.out_step)
         for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
 
-    const Phys<R> &ph = a.ph;
-    const Nodes<P, Q, R> &nd = a.nd;
-    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    P1Target<R> t;
+    t.khat = a.khat; t.N = a.N; t.ld = a.ld; t.Hnext = a.Hnext; t.qcount = a.qcount; t.queue = a.queue;
+    t.qoffset = 0u; t.key0 = a.key0; t.key1 = a.key1; t.stream_id = a.stream_id; t.step = a.step;
     unsigned int oog = 0u;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPT;
-
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT; base < a.N; base += stride) {
-        const int64_t i0 = base + (int64_t)threadIdx.x * PPT;
-        R cx[PPT][P], cy[PPT][P];
-        bool valid[PPT], finished[PPT];
-        const bool any = i0 < a.N;
-        if (any) {
-#pragma unroll
-            for (int h = 0; h < P; ++h) {
-                R vx[PPT], vy[PPT];
-                load_vec<R, PPT>(a.khat + (int64_t)h * a.ld + i0, vx);
-                load_vec<R, PPT>(a.khat + (int64_t)(P + h) * a.ld + i0, vy);
-#pragma unroll
-                for (int e = 0; e < PPT; ++e) { cx[e][h] = vx[e]; cy[e][h] = vy[e]; }
-            }
-            // drift (Eq. (17) / sG forcing term); the padding beyond N is left untouched
-#pragma unroll
-            for (int h = 0; h < P; ++h)
-                if (nd.drift_mask & (1u << h)) {
-                    R v[PPT];
-#pragma unroll
-                    for (int e = 0; e < PPT; ++e) {
-                        if (i0 + e < a.N) cx[e][h] -= nd.dhat[h];
-                        v[e] = cx[e][h];
-                    }
-                    store_vec<R, PPT>(a.khat + (int64_t)h * a.ld + i0, v);
-                }
-        }
-#pragma unroll
-        for (int e = 0; e < PPT; ++e) {
-            const int64_t i = i0 + e;
-            valid[e] = any && i < a.N;
-            finished[e] = false;
-            bool maybe = false;
-            if (valid[e]) {
-                // reconstruction, cells and the bound on the majorant
-                int rl[Q];   // cell (row << 16) | column; -1 outside the grid
-                R kkmax = (R)0;
-                recon_all(nd, cx[e], cy[e], [&](int q, R kx, R ky) {
-                    int r, l;
-                    rl[q] = cell_rl(ph, kx, ky, r, l) ? ((r << 16) | l) : -1;
-                    kkmax = fmax(kkmax, kx * kx + ky * ky);
-                });
-                const U4 r = philox4x32_10((uint32_t)i, a.stream_id, a.step, 0u, a.key0, a.key1);
-                const R lnxi = -rlog<R>(u01<R>(r.x));
-                const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
-                const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
-                maybe = lnxi < gub * ph.dt;
-                if (!maybe) {
-                    finished[e] = true;
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        if (rl[q] < 0) { ++oog; continue; }
-                        const int r = rl[q] >> 16, l = rl[q] & 0xffff;
-                        const int rr = r - a.win_r0, ll = l - a.win_r0;
-                        if (a.use_win && (unsigned)rr < (unsigned)kWin && (unsigned)ll < (unsigned)kWin)
-                            atomicAdd(&swin[q * kWinWords + rr * (kWin / 2) + (ll >> 1)], 1u << ((ll & 1) << 4));
-                        else
-                            atomicAdd(&a.Hnext[(int64_t)q * NN + r * ph.Nk + l], 1u);
-                    }
-                }
-            }
-            // colliders go to the queue (warp-aggregated append)
-            const unsigned int mask = __ballot_sync(0xffffffffu, maybe);
-            if (mask) {
-                const int leader = __ffs(mask) - 1;
-                uint32_t basepos = 0;
-                if (lane == leader) basepos = atomicAdd(a.qcount, (uint32_t)__popc(mask));
-                basepos = __shfl_sync(0xffffffffu, basepos, leader);
-                if (maybe) a.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)i;
-            }
-        }
-        if (a.out_step) {
-#pragma unroll 1
-            for (int q = 0; q < Q; ++q) {
-                R vx = (R)0, vy = (R)0, en = (R)0;
-#pragma unroll
-                for (int e = 0; e < PPT; ++e)
-                    if (finished[e]) {
-                        R kx, ky, a1, a2, a3;
-                        recon_node(nd, q, cx[e], cy[e], kx, ky);
-                        observe(ph, kx, ky, nd.eps0[q], a1, a2, a3);
-                        vx += a1; vy += a2; en += a3;
-                    }
-                vx = warp_sum(vx);
-                vy = warp_sum(vy);
-                en = warp_sum(en);
-                if (lane == 0) {
-                    smom[warp][q * 3 + 0] += (double)vx;
-                    smom[warp][q * 3 + 1] += (double)vy;
-                    smom[warp][q * 3 + 2] += (double)en;
-                }
-            }
-        }
-    }
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT; base < a.N; base += stride)
+        phase1_pass<P, Q, R>(a.ph, a.nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
+                             a.out_step != 0, smom[warp], oog);
     oog = warp_sum(oog);
     if (lane == 0 && oog) atomicAdd(&a.counters[4], (unsigned long long)oog);
     __syncthreads();
-    if (a.use_win) {  // flush the block's window: one global add per non-empty cell
-        for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) {
-            const uint32_t v = swin[j];
-            if (!v) continue;
-            const int q = j / kWinWords, w = j % kWinWords;
-            const int rr = w / (kWin / 2) + a.win_r0, ll = 2 * (w % (kWin / 2)) + a.win_r0;
-            uint32_t *base = a.Hnext + (int64_t)q * NN + (int64_t)rr * ph.Nk + ll;
-            if (v & 0xffffu) atomicAdd(base, v & 0xffffu);
-            if (v >> 16) atomicAdd(base + 1, v >> 16);
-        }
-    }
+    if (a.use_win) flush_window<Q>(swin, a.Hnext, a.ph.Nk, a.win_r0);
     if (a.out_step) {
         for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
             double s = 0.0;
@@ -378,11 +406,157 @@ __device__ __forceinline__ bool group_any(bool b, unsigned mask)
     return (__ballot_sync(mask, b) & mask) != 0u;
 }
 
+// Everything the collision loop of one particle needs about its ensemble.
+template <typename R>
+struct P2Target {
+    R *khat;
+    int64_t ld;
+    const uint32_t *Hcur;     // f^n
+    uint32_t *Hnext;          // f^{n+1}
+    const uint32_t *nmax;
+    double *mom;              // [Q*3] moment accumulators (shared or global), on moment steps
+    uint32_t key0, key1, stream_id, step;
+    bool out_step;
+};
+
+struct P2Counts { unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0; };
+
+// The collision loop of Algorithm 1 / 2 for particle i, carried by the G lanes of a group (lane r
+// owns nodes r, r + G, ...), then the histogram f^{n+1} and moments of its final state.
+template <int P, int Q, typename R>
+__device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const P2Target<R> &t,
+                                                 int64_t i, int r, unsigned gmask, P2Counts &cnt)
+{
+    constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
+    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
+    R cx[P], cy[P], kx[NPL], ky[NPL];
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+        cx[h] = t.khat[(int64_t)h * t.ld + i];
+        cy[h] = t.khat[(int64_t)(P + h) * t.ld + i];
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const int q = r + s * G;
+        if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+    }
+    auto majorant = [&]() {
+        R gm = (R)0;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q < Q) {
+                R g[6];
+                gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], g));
+            }
+        }
+        return ph.alpha1 * group_max<G>(gm, gmask);
+    };
+    R Gt = majorant();
+    R tc = (R)0;
+    uint32_t c = 0;
+    U4 rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
+    R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
+    bool touched = false;
+    while (tc + dtc < ph.dt) {               // group-uniform condition
+        if ((int)c >= ph.max_coll) { if (r == 0) ++cnt.cap; break; }
+        if (r == 0) ++cnt.att;
+        touched = true;
+        EventAngles<R> ang;
+        ang.reset(u01<R>(rr.w));
+        const R target = u01<R>(rr.y) * Gt;
+        bool changed = false;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q >= Q) continue;
+            R g[6];
+            rates6(ph, kx[s], ky[s], nd.eps0[q], g);
+            int l = 6;
+            R cum = (R)0;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                cum += g[m];
+                if (l == 6 && target < cum) l = m;
+            }
+            if (l == 6) continue;  // self scattering: h^7 = identity
+            R nkx, nky;
+            final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
+            bool accept = true;
+            if (ph.pauli_mode != 2) {
+                const int cl = cell_of(ph, nkx + nd.dq[q], nky);
+                if (cl >= 0) accept = pauli_accept(t.Hcur[(int64_t)q * NN + cl], t.nmax[q], rr.z);
+            }
+            if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
+            else ++cnt.rej;
+        }
+        if (group_any<G>(changed, gmask) && r == 0) ++cnt.chg;
+        // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            R sx = (R)0, sy = (R)0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) {
+                    sx += nd.wpsi[q * P + h] * kx[s];
+                    sy += nd.wpsi[q * P + h] * ky[s];
+                }
+            }
+            cx[h] = group_sum<G>(sx, gmask);
+            cy[h] = group_sum<G>(sy, gmask);
+        }
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+        }
+        Gt = majorant();
+        tc += dtc;
+        ++c;
+        rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
+        dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
+    }
+    if (touched) {
+        // lane h of the group writes coefficient h (x and y planes)
+        for (int h = r; h < P; h += G) {
+            R vx = cx[0], vy = cy[0];
+#pragma unroll
+            for (int hh = 0; hh < P; ++hh) if (hh == h) { vx = cx[hh]; vy = cy[hh]; }
+            t.khat[(int64_t)h * t.ld + i] = vx;
+            t.khat[(int64_t)(P + h) * t.ld + i] = vy;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const int q = r + s * G;
+        if (q >= Q) continue;
+        const int cl = cell_of(ph, kx[s], ky[s]);
+        if (cl >= 0) atomicAdd(&t.Hnext[(int64_t)q * NN + cl], 1u);
+        else ++cnt.oog;
+        if (t.out_step) {
+            R vx, vy, e;
+            observe(ph, kx[s], ky[s], nd.eps0[q], vx, vy, e);
+            atomicAdd(&t.mom[q * 3 + 0], (double)vx);
+            atomicAdd(&t.mom[q * 3 + 1], (double)vy);
+            atomicAdd(&t.mom[q * 3 + 2], (double)e);
+        }
+    }
+}
+
+// Copy a trivially-copyable table into shared memory (all threads; caller synchronises).
+template <typename T>
+__device__ __forceinline__ void stage(uint32_t *dst, const T &src)
+{
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+    for (int j = threadIdx.x; j < (int)(sizeof(T) / 4); j += blockDim.x) dst[j] = s[j];
+}
+
 template <int P, int Q, typename R>
 __global__ void __launch_bounds__(kPhase2Threads)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
-    constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
+    constexpr int G = GroupOf<Q>::G;
     __shared__ double smom[Q * 3];
     __shared__ unsigned long long scnt[5];
     // The lanes of a group read different nodes' tables: staged in shared memory (the constant
@@ -391,143 +565,30 @@ k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
     __shared__ __align__(16) uint32_t snd[(sizeof(Nodes<P, Q, R>) + 3) / 4];
     if (threadIdx.x < 5) scnt[threadIdx.x] = 0ull;
     for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) smom[j] = 0.0;
-    {
-        const uint32_t *s1 = reinterpret_cast<const uint32_t *>(&a.ph);
-        for (int j = threadIdx.x; j < (int)(sizeof(Phys<R>) / 4); j += blockDim.x) sph[j] = s1[j];
-        const uint32_t *s2 = reinterpret_cast<const uint32_t *>(&a.nd);
-        for (int j = threadIdx.x; j < (int)(sizeof(Nodes<P, Q, R>) / 4); j += blockDim.x) snd[j] = s2[j];
-    }
+    stage(sph, a.ph);
+    stage(snd, a.nd);
     __syncthreads();
 
     const Phys<R> &ph = *reinterpret_cast<const Phys<R> *>(sph);
     const Nodes<P, Q, R> &nd = *reinterpret_cast<const Nodes<P, Q, R> *>(snd);
-    const int64_t NN = (int64_t)ph.Nk * ph.Nk;
     const uint32_t count = *a.qcount;
-    unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0;
+    P2Counts cnt;
+    P2Target<R> t;
+    t.khat = a.khat; t.ld = a.ld; t.Hcur = a.Hcur; t.Hnext = a.Hnext; t.nmax = a.nmax; t.mom = smom;
+    t.key0 = a.key0; t.key1 = a.key1; t.stream_id = a.stream_id; t.step = a.step; t.out_step = a.out_step != 0;
 
     const int lane = threadIdx.x & 31;
     const int r = lane % G;                                  // lane in the group
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
     const uint32_t gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     const uint32_t ngroups = gridDim.x * blockDim.x / G;
+    for (uint32_t j = gid; j < count; j += ngroups) collide_particle<P, Q, R>(ph, nd, t, a.queue[j], r, gmask, cnt);
 
-    for (uint32_t j = gid; j < count; j += ngroups) {
-        const int64_t i = a.queue[j];
-        R cx[P], cy[P], kx[NPL], ky[NPL];
-        load_coeffs(a, i, cx, cy);
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int q = r + s * G;
-            if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
-        }
-        auto majorant = [&]() {
-            R gm = (R)0;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) {
-                    R g[6];
-                    gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], g));
-                }
-            }
-            return ph.alpha1 * group_max<G>(gm, gmask);
-        };
-        R Gt = majorant();
-        R tc = (R)0;
-        uint32_t c = 0;
-        U4 rr = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
-        R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
-        bool touched = false;
-        while (tc + dtc < ph.dt) {               // group-uniform condition
-            if ((int)c >= ph.max_coll) { if (r == 0) ++cap; break; }
-            if (r == 0) ++att;
-            touched = true;
-            EventAngles<R> ang;
-            ang.reset(u01<R>(rr.w));
-            const R target = u01<R>(rr.y) * Gt;
-            bool changed = false;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q >= Q) continue;
-                R g[6];
-                rates6(ph, kx[s], ky[s], nd.eps0[q], g);
-                int l = 6;
-                R cum = (R)0;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    cum += g[m];
-                    if (l == 6 && target < cum) l = m;
-                }
-                if (l == 6) continue;  // self scattering: h^7 = identity
-                R nkx, nky;
-                final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
-                bool accept = true;
-                if (ph.pauli_mode != 2) {
-                    const int cl = cell_of(ph, nkx + nd.dq[q], nky);
-                    if (cl >= 0) accept = pauli_accept(a.Hcur[(int64_t)q * NN + cl], a.nmax[q], rr.z);
-                }
-                if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
-                else ++rej;
-            }
-            if (group_any<G>(changed, gmask) && r == 0) ++chg;
-            // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
-#pragma unroll
-            for (int h = 0; h < P; ++h) {
-                R sx = (R)0, sy = (R)0;
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    const int q = r + s * G;
-                    if (q < Q) {
-                        sx += nd.wpsi[q * P + h] * kx[s];
-                        sy += nd.wpsi[q * P + h] * ky[s];
-                    }
-                }
-                cx[h] = group_sum<G>(sx, gmask);
-                cy[h] = group_sum<G>(sy, gmask);
-            }
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
-            }
-            Gt = majorant();
-            tc += dtc;
-            ++c;
-            rr = philox4x32_10((uint32_t)i, a.stream_id, a.step, c, a.key0, a.key1);
-            dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
-        }
-        if (touched) {
-            // lane h of the group writes coefficient h (x and y planes)
-            for (int h = r; h < P; h += G) {
-                R vx = cx[0], vy = cy[0];
-#pragma unroll
-                for (int hh = 0; hh < P; ++hh) if (hh == h) { vx = cx[hh]; vy = cy[hh]; }
-                a.khat[(int64_t)h * a.ld + i] = vx;
-                a.khat[(int64_t)(P + h) * a.ld + i] = vy;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int q = r + s * G;
-            if (q >= Q) continue;
-            const int cl = cell_of(ph, kx[s], ky[s]);
-            if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
-            else ++oog;
-            if (a.out_step) {
-                R vx, vy, e;
-                observe(ph, kx[s], ky[s], nd.eps0[q], vx, vy, e);
-                atomicAdd(&smom[q * 3 + 0], (double)vx);
-                atomicAdd(&smom[q * 3 + 1], (double)vy);
-                atomicAdd(&smom[q * 3 + 2], (double)e);
-            }
-        }
-    }
-    if (att) atomicAdd(&scnt[0], att);
-    if (chg) atomicAdd(&scnt[1], chg);
-    if (rej) atomicAdd(&scnt[2], rej);
-    if (cap) atomicAdd(&scnt[3], cap);
-    if (oog) atomicAdd(&scnt[4], oog);
+    if (cnt.att) atomicAdd(&scnt[0], cnt.att);
+    if (cnt.chg) atomicAdd(&scnt[1], cnt.chg);
+    if (cnt.rej) atomicAdd(&scnt[2], cnt.rej);
+    if (cnt.cap) atomicAdd(&scnt[3], cnt.cap);
+    if (cnt.oog) atomicAdd(&scnt[4], cnt.oog);
     __syncthreads();
     if (threadIdx.x < 5 && scnt[threadIdx.x]) atomicAdd(&a.counters[threadIdx.x], scnt[threadIdx.x]);
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&a.counters[5], (unsigned long long)count);

@@ -72,6 +72,13 @@ Runner *make_runner_1x1(int precision, const HostTables &t, const DevBuffers &b,
 Runner *make_runner_6x6(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
 Runner *make_runner_21x36(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
 
+struct BatchCase;
+struct BatchScratch;
+class BatchRunner;
+BatchRunner *make_batch_runner(int P, int Q, int precision, const std::vector<BatchCase> &cases,
+                               const BatchScratch &sc, int num_sms);
+size_t case_dev_size(int P, int Q, int precision);
+
 // Launch accounting (every kernel launch of the library increments it).
 void count_launch(uint64_t n = 1);
 

@@ -71,6 +71,7 @@ public:
     }
 
     int grid1() const override { return grid1_; }
+    const StepArgs<P, Q, R> &args() const { return args_; }
 
     cudaError_t init_sample(cudaStream_t s) override
     {

@@ -71,6 +71,12 @@ SIGNATURES = {
     "pgc_profile": (C.c_int, [_vp, C.c_int32]),
     "pgc_profile_read": (C.c_int, [_vp, _dp, _dp, _i64p]),
     "pgc_observe_static": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "pgc_batch_query_sizes": (C.c_int, [C.POINTER(_vp), C.c_int32, C.POINTER(C.c_size_t)]),
+    "pgc_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int32, _vp, C.c_int32, C.POINTER(_vp)]),
+    "pgc_batch_step": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32]),
+    "pgc_batch_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _dp]),
+    "pgc_batch_destroy": (None, [_vp]),
+    "pgc_batch_last_error": (C.c_char_p, [_vp]),
     "pgc_destroy": (None, [_vp]),
     "pgc_last_error": (C.c_char_p, [_vp]),
     "pgc_status_string": (C.c_char_p, [C.c_int]),
@@ -195,6 +201,42 @@ def pgc_observe_static(ctx, d_hist_out: int, d_record_out: int, stream: int = 0)
     _check(lib().pgc_observe_static(_vp(ctx), _vp(d_hist_out), _vp(d_record_out), _vp(stream)), _vp(ctx))
 
 
+def _check_batch(status, b=None):
+    if status != PGC_OK:
+        msg = lib().pgc_batch_last_error(b)
+        raise PgcError(status, msg.decode() if msg else "")
+
+
+def pgc_batch_query_sizes(ctxs):
+    arr = (_vp * len(ctxs))(*ctxs)
+    n = C.c_size_t()
+    _check_batch(lib().pgc_batch_query_sizes(arr, len(ctxs), C.byref(n)))
+    return n.value
+
+
+def pgc_batch_create(ctxs, d_scratch: int, tile: int = 0):
+    arr = (_vp * len(ctxs))(*ctxs)
+    out = _vp()
+    _check_batch(lib().pgc_batch_create(arr, len(ctxs), _vp(d_scratch), int(tile), C.byref(out)))
+    return out.value
+
+
+def pgc_batch_step(b, n_steps: int, moments_every: int = 0, use_graph: bool = True):
+    _check_batch(lib().pgc_batch_step(_vp(b), int(n_steps), int(moments_every), int(bool(use_graph))), _vp(b))
+
+
+def pgc_batch_autotune(b, steps_per_candidate: int):
+    t = C.c_int32()
+    ms = C.c_double()
+    _check_batch(lib().pgc_batch_autotune(_vp(b), int(steps_per_candidate), C.byref(t), C.byref(ms)), _vp(b))
+    return t.value, ms.value
+
+
+def pgc_batch_destroy(b):
+    if b:
+        lib().pgc_batch_destroy(_vp(b))
+
+
 def pgc_destroy(ctx):
     if ctx:
         lib().pgc_destroy(_vp(ctx))
@@ -297,3 +339,38 @@ class Simulation:
 
     def reconstruct_f(self, z):
         return pgc_reconstruct_f(self.ctx, z, self.d, self.Nk)
+
+
+class BatchSimulation:
+    """Many cases advanced together (pgc_batch_*).  Each case is a Simulation on one dedicated
+    (non-default) stream, so that the step sequence can be captured into a CUDA graph."""
+
+    def __init__(self, cases, max_outputs: int = 1024, tile: int = 0, stream=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.sims = [Simulation(p, max_outputs=max_outputs, stream=self.stream) for p in cases]
+        ctxs = [s.ctx for s in self.sims]
+        n = pgc_batch_query_sizes(ctxs)
+        self.scratch_buf = torch.empty(max(n, 256), dtype=torch.uint8, device=self.sims[0].state_buf.device)
+        self.batch = pgc_batch_create(ctxs, self.scratch_buf.data_ptr(), tile)
+
+    def step(self, n_steps: int, moments_every: int = 0, use_graph: bool = True):
+        pgc_batch_step(self.batch, n_steps, moments_every, use_graph)
+
+    def autotune(self, steps_per_candidate: int = 3):
+        return pgc_batch_autotune(self.batch, steps_per_candidate)
+
+    def close(self):
+        if getattr(self, "batch", None):
+            pgc_batch_destroy(self.batch)
+            self.batch = None
+        for s in getattr(self, "sims", []):
+            s.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,101 @@
+"""Batched sweep (pgc_batch_*): every case of a batch follows exactly the trajectory of its
+standalone run (same Philox streams, same arithmetic), with and without CUDA-graph replay and
+for any tile size the autotuner picks."""
+import numpy as np
+import pytest
+
+from paper_2404_19602_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_19602_gb300 import build
+
+    build.build()
+
+
+def _cases(prec, base=W.GAP_UQ_1E6, ns=(3000, 5000, 1000, 7001)):
+    out = []
+    for c, n in enumerate(ns):
+        E = 1000.0 + 6000.0 * c
+        w = 0.02 + 0.05 * c
+        out.append(W.scaled(base, N=n, Ex_lo=E, Ex_hi=E, eps0_lo=0.1 - w / 4, eps0_hi=0.1 + w / 4,
+                            precision=prec, stream_id=c, seed=7))
+    return out
+
+
+def _single(p, steps, every):
+    from paper_2404_19602_gb300 import pgc
+
+    s = pgc.Simulation(p, max_outputs=steps // max(every, 1) + 2)
+    s.step(steps, every)
+    return s.state(), s.moments(), s.hist()[0], s.counters()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_cases_equal_standalone_runs(prec, use_graph):
+    from paper_2404_19602_gb300 import pgc
+
+    cases = _cases(prec)
+    steps, every = 40, 10
+    b = pgc.BatchSimulation(cases, max_outputs=steps // every + 2, tile=2048)
+    b.step(steps, every, use_graph=use_graph)
+    torch.cuda.synchronize()
+    rtol = 1e-9 if prec == "fp64" else 1e-5
+    for p, sim in zip(cases, b.sims):
+        ks, ms, hs, cs = _single(p, steps, every)
+        assert np.array_equal(sim.state(), ks), p["stream_id"]
+        assert np.array_equal(sim.hist()[0], hs), p["stream_id"]
+        mb = sim.moments()
+        assert np.array_equal(mb["t_fs"], ms["t_fs"])
+        assert np.allclose(mb["nodes"], ms["nodes"], rtol=rtol, atol=0)
+        cb = sim.counters()
+        for k in ("attempts", "changed", "rejected", "capped", "steps"):
+            assert cb[k] == cs[k], (k, cb[k], cs[k])
+    b.close()
+
+
+def test_batch_autotune_keeps_trajectories():
+    from paper_2404_19602_gb300 import pgc
+
+    cases = _cases("fp32")
+    b = pgc.BatchSimulation(cases, max_outputs=8)
+    tile, ms = b.autotune(2)
+    assert tile % 1024 == 0 and ms > 0
+    steps = sum(1 for t in range(1024, 32769) if t & (t - 1) == 0) * 2  # candidates x 2 steps
+    b.step(10, 0)
+    torch.cuda.synchronize()
+    for p, sim in zip(cases, b.sims):
+        ks, _, hs, _ = _single(p, steps + 10, 0)
+        assert np.array_equal(sim.state(), ks)
+        assert np.array_equal(sim.hist()[0], hs)
+    b.close()
+
+
+def test_batch_two_random_inputs_fp64():
+    from paper_2404_19602_gb300 import pgc
+
+    cases = [W.scaled(W.GAP_FIELD_UQ_4E6, N=n, precision="fp64", stream_id=c) for c, n in enumerate((600, 257))]
+    b = pgc.BatchSimulation(cases, max_outputs=4, tile=512)
+    b.step(12, 6)
+    torch.cuda.synchronize()
+    for p, sim in zip(cases, b.sims):
+        ks, ms, hs, _ = _single(p, 12, 6)
+        assert np.array_equal(sim.state(), ks)
+        assert np.allclose(sim.moments()["nodes"], ms["nodes"], rtol=1e-9, atol=0)
+    b.close()
+
+
+def test_batch_rejects_mismatched_cases():
+    from paper_2404_19602_gb300 import pgc
+
+    a = pgc.Simulation(W.scaled(W.GAP_UQ_1E6, N=100))
+    c = pgc.Simulation(W.scaled(W.GAP_UQ_1E6, N=100, precision="fp64"))
+    with pytest.raises(pgc.PgcError):
+        pgc.pgc_batch_query_sizes([a.ctx, c.ctx])
