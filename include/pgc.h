@@ -237,6 +237,26 @@ pgc_status pgc_batch_autotune(pgc_batch *b, int32_t steps_per_candidate, int32_t
 void pgc_batch_destroy(pgc_batch *b);
 const char *pgc_batch_last_error(const pgc_batch *b);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Adjoint: pathwise sensitivities (discrete events frozen) of the time-averaged mean and      */
+/* variance over z of the current J_x.                                                        */
+/*   Jbar = average over the moment records n in (n_steps - window_steps, n_steps] of mean_z J_x,*/
+/*   Vbar = the same average of var_z J_x;  L = w[0] Jbar + w[1] Vbar.                        */
+/* Gradient of L with respect to theta = (E_lo, E_hi, eps0_lo, eps0_hi), the endpoints of the   */
+/* field and band-minimum intervals (for a deterministic input each endpoint derivative is half */
+/* of the derivative with respect to the common value).  The context must be at step 0 with its */
+/* sampled initial state.  pgc_adjoint runs the forward n_steps exactly as pgc_step (the context */
+/* and its moment series advance), keeping a checkpoint (state + histogram) every ckpt_every   */
+/* steps, then the reverse sweep: each segment is replayed with the forward kernels and walked  */
+/* backwards (transposed Jacobians of drift, reconstruction, final-state maps and projection,  */
+/* moment terms), ending with the sensitivity of the Fermi-Dirac sampling.                     */
+/* Work memory (caller-owned device buffer) from pgc_adjoint_query_sizes.                      */
+/* Supported: the paper's final states; Pauli initial-maximum or off.                          */
+/* ---------------------------------------------------------------------------------------- */
+pgc_status pgc_adjoint_query_sizes(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, size_t *work_bytes);
+pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_t moments_every, int64_t window_steps,
+                       const double *h_weights, void *d_work, double *h_value, double *h_grad);
+
 /* Number of kernel launches issued by the library since load (for launch accounting). */
 uint64_t pgc_launch_count(void);
 

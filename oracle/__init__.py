@@ -106,6 +106,10 @@ def lib():
             L.orc_angle_k.argtypes = [C.c_double]
             L.orc_project_nodes.argtypes = [vp, dp, dp]
             L.orc_recon_nodes.argtypes = [vp, dp, dp]
+            L.orc_tangent_run.restype = C.c_int
+            L.orc_tangent_run.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, dp, dp]
+            L.orc_window_objective.restype = C.c_int
+            L.orc_window_objective.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -301,6 +305,23 @@ class Oracle:
         out = np.zeros(self.Q)
         lib().orc_recon_nodes(self._h, _dp(vhat), _dp(out))
         return out
+
+    def tangent_run(self, nsteps, every, window):
+        """Pathwise sensitivities (events frozen) of the window averages of mean_z J_x and
+        var_z J_x with respect to (E_lo, E_hi, eps0_lo, eps0_hi); advances the state."""
+        val = np.zeros(2)
+        grad = np.zeros(8)
+        r = lib().orc_tangent_run(self._h, int(nsteps), int(every), int(window), _dp(val), _dp(grad))
+        if r != 0:
+            raise RuntimeError("orc_tangent_run failed (%d)" % r)
+        return val, grad.reshape(2, 4)
+
+    def window_objective(self, nsteps, every, window):
+        val = np.zeros(2)
+        r = lib().orc_window_objective(self._h, int(nsteps), int(every), int(window), _dp(val))
+        if r != 0:
+            raise RuntimeError("orc_window_objective failed (%d)" % r)
+        return val
 
     def observe_at(self, z):
         z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.float64)

@@ -324,6 +324,7 @@ typedef struct {
     uint32_t *Nmax;    /* [Q] normaliser of the Pauli test */
     int64_t *cellbuf;  /* [N][Q] scratch */
     int64_t step;
+    int sampled;       /* 1 if the state came from the Fermi-Dirac sampling of orc_init */
     /* counters */
     int64_t n_coll_attempts, n_real, n_rejected, n_capped, n_out_of_grid;
     /* time series */
@@ -683,6 +684,7 @@ int orc_init(void *st, const double *h_khat)
     const orc_cfg *c = &S->cfg;
     int P = S->P, Q = S->Q;
     int64_t N = c->N;
+    S->sampled = (h_khat == NULL);
     if (h_khat) memcpy(S->khat, h_khat, sizeof(double) * 2 * (size_t)P * N);
     else {
 #pragma omp parallel for schedule(static)
@@ -1024,4 +1026,319 @@ int orc_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Pathwise sensitivities by forward-mode tangents (test reference for the adjoint).          */
+/*                                                                                            */
+/* theta = (E_lo, E_hi, eps0_lo, eps0_hi): the endpoints of the field and band-minimum         */
+/* intervals; for a deterministic input the two endpoint derivatives are each half of the      */
+/* derivative with respect to the common value (the affine map at z = 0).  Discrete events     */
+/* (collision times, mechanisms, Pauli outcomes, the trapezoid segment of the edge angle, the   */
+/* histogram cells) are frozen at those of the primal run; the random numbers are common.      */
+/* Derivatives are propagated through: the Fermi-Dirac sampling (implicit derivative of the    */
+/* inverse CDF), the drift (Eq. 17 / Sec. 4.1), the final-state maps h^1..h^6 of Sec. 3, the   */
+/* projections (Eqs. 28-30) and the observables (Eqs. 35-37, with n(eps0) of Eq. 31).          */
+/* ------------------------------------------------------------------------------------------ */
+#define NTH 4
+
+/* parameter derivatives of the node's band minimum and field */
+static void node_param_derivs(const orc_state *S, int q, double de0[NTH], double dE[NTH])
+{
+    const orc_cfg *c = &S->cfg;
+    int eps_random = (c->eps0_lo != c->eps0_hi), E_random = (c->Ex_lo != c->Ex_hi);
+    double z1 = 0.0, z2 = 0.0;
+    if (S->d == 1) { if (eps_random) z1 = S->zq[q]; else z2 = S->zq[q]; }
+    if (S->d == 2) { z1 = S->zq[2 * q]; z2 = S->zq[2 * q + 1]; }
+    (void)E_random;
+    for (int t = 0; t < NTH; ++t) { de0[t] = 0.0; dE[t] = 0.0; }
+    dE[0] = 0.5 * (1.0 - z2);
+    dE[1] = 0.5 * (1.0 + z2);
+    de0[2] = 0.5 * (1.0 - z1);
+    de0[3] = 0.5 * (1.0 + z1);
+}
+
+static double rho_fd(double e, double mu, double kT) { return e / (1.0 + exp(fmin((e - mu) / kT, 700.0))); }
+
+/* edge angle (same operations as orc_angle_edge) and its derivatives in beta and c */
+static double edge_angle_grad(double beta, double cth, double u, int n, double *dth_db, double *dth_dc)
+{
+    double h = 2.0 * ORC_PI / n;
+    double *C = (double *)malloc(sizeof(double) * 3 * (size_t)(n + 1));
+    double *Cb = C + (n + 1), *Cc = Cb + (n + 1);
+    double x0 = 1.0 - cth;
+    double gprev = exp(-beta * x0 * x0), gbp = -x0 * x0 * gprev, gcp = 2.0 * beta * x0 * gprev;
+    C[0] = Cb[0] = Cc[0] = 0.0;
+    for (int j = 1; j <= n; ++j) {
+        double x = cos(j * h) - cth;
+        double g = exp(-beta * x * x), gb = -x * x * g, gc = 2.0 * beta * x * g;
+        C[j] = C[j - 1] + 0.5 * h * (gprev + g);
+        Cb[j] = Cb[j - 1] + 0.5 * h * (gbp + gb);
+        Cc[j] = Cc[j - 1] + 0.5 * h * (gcp + gc);
+        gprev = g; gbp = gb; gcp = gc;
+    }
+    double target = u * C[n];
+    int j = 0;
+    while (j < n - 1 && C[j + 1] <= target) ++j;
+    double D = C[j + 1] - C[j], f = (target - C[j]) / D;
+    double Db = Cb[j + 1] - Cb[j], Dc = Cc[j + 1] - Cc[j];
+    double fb = ((u * Cb[n] - Cb[j]) * D - (target - C[j]) * Db) / (D * D);
+    double fc = ((u * Cc[n] - Cc[j]) * D - (target - C[j]) * Dc) / (D * D);
+    free(C);
+    *dth_db = fb * h;
+    *dth_dc = fc * h;
+    return (j + f) * h;
+}
+
+/* Jacobian dk'/dk (row-major 2x2) of the final-state map of mechanism l (0..5), random numbers
+ * fixed, paper final states. */
+static void fs_jacobian(const orc_state *S, int l, double kx, double ky, double uth, double J[4])
+{
+    double km = sqrt(kx * kx + ky * ky);
+    if (l == 5) {
+        double cth = (km > 0.0) ? kx / km : 1.0;
+        double beta = 2.0 * km * km * S->a_nm * S->a_nm;
+        double db, dc;
+        double th = edge_angle_grad(beta, cth, uth, S->cfg.n_theta, &db, &dc);
+        double ct = cos(th), st = sin(th);
+        double nx = (km > 0.0) ? kx / km : 1.0, ny = (km > 0.0) ? ky / km : 0.0;
+        double gbx = 4.0 * S->a_nm * S->a_nm * kx, gby = 4.0 * S->a_nm * S->a_nm * ky; /* d beta / dk */
+        double gcx = 0.0, gcy = 0.0;                                                    /* d c / dk */
+        if (km > 0.0) { gcx = ky * ky / (km * km * km); gcy = -kx * ky / (km * km * km); }
+        double tx = db * gbx + dc * gcx, ty = db * gby + dc * gcy;                      /* d th / dk */
+        J[0] = ct * nx - km * st * tx; J[1] = ct * ny - km * st * ty;
+        J[2] = st * nx + km * ct * tx; J[3] = st * ny + km * ct * ty;
+        return;
+    }
+    double th, s = 0.0, dlt = 0.0;
+    if (l == 0) th = orc_angle_ac(uth);
+    else if (l == 1 || l == 2) { th = 2.0 * ORC_PI * uth; dlt = S->hwO / S->hvF; s = (l == 1) ? -1.0 : 1.0; }
+    else { th = orc_angle_k(uth); dlt = S->hwK / S->hvF; s = (l == 3) ? -1.0 : 1.0; }
+    double ct = cos(th), st = sin(th);
+    /* k' = R k (1 + s dlt/|k|):  dk'/dk = R [ (1 + s dlt/|k|) I - (s dlt/|k|) n n^T ] */
+    double a = 1.0 + s * dlt / km, b = s * dlt / km;
+    double nx = kx / km, ny = ky / km;
+    double M0 = a - b * nx * nx, M1 = -b * nx * ny, M2 = -b * ny * nx, M3 = a - b * ny * ny;
+    J[0] = ct * M0 - st * M2; J[1] = ct * M1 - st * M3;
+    J[2] = st * M0 + ct * M2; J[3] = st * M1 + ct * M3;
+}
+
+/* node observables and their tangents at the current state: J[q], dJ[q][t] */
+static void tangent_observe(const orc_state *S, const double *dk, double *Jq, double *dJq)
+{
+    int P = S->P, Q = S->Q;
+    int64_t N = S->cfg.N;
+    double vF_ms = T1_VF_CMS * 1e-2;
+    for (int q = 0; q < Q; ++q) {
+        double e0 = S->eps0q[q], de0[NTH], dE[NTH];
+        node_param_derivs(S, q, de0, dE);
+        double sv = 0.0, sdv[NTH] = {0, 0, 0, 0};
+        for (int64_t i = 0; i < N; ++i) {
+            double kx = 0.0, ky = 0.0;
+            for (int h = 0; h < P; ++h) { kx += khat_at(S, 0, h, i) * S->psi[q * P + h]; ky += khat_at(S, 1, h, i) * S->psi[q * P + h]; }
+            double eps = sqrt(S->hvF * S->hvF * (kx * kx + ky * ky) + e0 * e0);
+            double v = S->hvF * kx / eps;
+            double e3 = eps * eps * eps;
+            double dvdkx = S->hvF / eps - S->hvF * S->hvF * S->hvF * kx * kx / e3;
+            double dvdky = -S->hvF * S->hvF * S->hvF * kx * ky / e3;
+            double dvde0 = -S->hvF * kx * e0 / e3;
+            sv += v;
+            for (int t = 0; t < NTH; ++t) {
+                double dkx = 0.0, dky = 0.0;
+                for (int h = 0; h < P; ++h) {
+                    dkx += dk[(((size_t)t * 2 + 0) * P + h) * N + i] * S->psi[q * P + h];
+                    dky += dk[(((size_t)t * 2 + 1) * P + h) * N + i] * S->psi[q * P + h];
+                }
+                sdv[t] += dvdkx * dkx + dvdky * dky + dvde0 * de0[t];
+            }
+        }
+        double nq = S->nq[q];
+        double dn = -2.0 / (ORC_PI * S->hvF * S->hvF) * rho_fd(e0, S->cfg.eps_F, S->kT) * 1e18;
+        Jq[q] = -Q_E * nq * vF_ms * sv / (double)N;
+        for (int t = 0; t < NTH; ++t)
+            dJq[q * NTH + t] = -Q_E * vF_ms / (double)N * (dn * de0[t] * sv + nq * sdv[t]);
+    }
+}
+
+int orc_tangent_run(void *st, int64_t nsteps, int64_t every, int64_t window, double *val2, double *grad8)
+{
+    orc_state *S = (orc_state *)st;
+    const orc_cfg *c = &S->cfg;
+    if (!S->sampled || S->step != 0 || c->final_state != ORC_FS_PAPER || every < 1) return -1;
+    int P = S->P, Q = S->Q;
+    int64_t N = c->N;
+    double *dk = (double *)calloc((size_t)NTH * 2 * P * N, sizeof(double));
+    /* initial tangents: k_q = |k|(cos th, sin th), |k| = sqrt(eps^2 - e0^2)/hvF, eps = F^-1(u; e0) */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        uint32_t ctr[4] = {(uint32_t)i, c->stream_id, 0u, ORC_INIT_PURPOSE};
+        uint32_t key[2] = {(uint32_t)c->seed, (uint32_t)(c->seed >> 32)};
+        uint32_t o[4];
+        orc_philox(ctr, key, o);
+        double ue = orc_u01(o[0]), th = 2.0 * ORC_PI * orc_u01(o[1]);
+        for (int q = 0; q < Q; ++q) {
+            double e0 = S->eps0q[q], de0[NTH], dE[NTH];
+            node_param_derivs(S, q, de0, dE);
+            double eps = orc_fd_sample(e0, c->eps_F, S->kT, ue);
+            double r = eps * eps - e0 * e0;
+            if (r <= 0.0) continue;
+            double km = sqrt(r) / S->hvF;
+            double deps = rho_fd(e0, c->eps_F, S->kT) * (1.0 - ue) / rho_fd(eps, c->eps_F, S->kT);
+            double dkm = (eps * deps - e0) / (S->hvF * S->hvF * km);
+            for (int t = 0; t < NTH; ++t)
+                for (int h = 0; h < P; ++h) {
+                    double wp = S->wq[q] * S->psi[q * P + h];
+                    dk[(((size_t)t * 2 + 0) * P + h) * N + i] += wp * dkm * de0[t] * cos(th);
+                    dk[(((size_t)t * 2 + 1) * P + h) * N + i] += wp * dkm * de0[t] * sin(th);
+                }
+        }
+    }
+    /* per-step drift derivative of the x coefficients: d dhat_h / d theta */
+    double ddhat[NTH * 64];
+    for (int t = 0; t < NTH; ++t)
+        for (int h = 0; h < P; ++h) {
+            double sacc = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                double de0[NTH], dE[NTH];
+                node_param_derivs(S, q, de0, dE);
+                sacc += S->wq[q] * S->psi[q * P + h] * dE[t] * 1e-7 * c->dt_fs / S->hbar_fs;
+            }
+            ddhat[t * 64 + h] = sacc;
+        }
+    double accJ = 0.0, accV = 0.0, accdJ[NTH] = {0, 0, 0, 0}, accdV[NTH] = {0, 0, 0, 0};
+    int64_t nout = 0;
+    double *Jq = (double *)calloc((size_t)Q, sizeof(double)), *dJq = (double *)calloc((size_t)Q * NTH, sizeof(double));
+    for (int64_t n = 0; n < nsteps; ++n) {
+        const uint32_t *Hn = S->H;
+        uint32_t Nmx[1296];
+        if (c->pauli_norm == ORC_PAULI_CURRENT_MAX) hist_max(S, Nmx);
+        else memcpy(Nmx, S->Nmax, sizeof(uint32_t) * Q);
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < N; ++i) {
+            double kx[1296], ky[1296], g[1296 * 6];
+            double *tk = (double *)malloc(sizeof(double) * NTH * 2 * (size_t)Q);  /* node tangents */
+            int64_t rej = 0;
+            for (int h = 0; h < P; ++h) {
+                S->khat[((size_t)0 * P + h) * N + i] -= S->dhat[h];
+                for (int t = 0; t < NTH; ++t) dk[(((size_t)t * 2 + 0) * P + h) * N + i] -= ddhat[t * 64 + h];
+            }
+            recon_particle(S, i, kx, ky);
+            double Gt = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                orc_rates_node(S, kx[q], ky[q], S->eps0q[q], &g[q * 6]);
+                double sg = 0.0;
+                for (int m = 0; m < 6; ++m) sg += g[q * 6 + m];
+                if (sg > Gt) Gt = sg;
+            }
+            Gt *= (1.0 + c->alpha);
+            double tc = 0.0, u[4];
+            uint32_t cc = 0;
+            orc_draw(c, i, n, cc, u);
+            double dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY;
+            while (tc + dtc < c->dt_fs) {
+                if ((int)cc >= c->max_coll) break;
+                /* node tangents of the current state */
+                for (int q = 0; q < Q; ++q)
+                    for (int t = 0; t < NTH; ++t) {
+                        double ax = 0.0, ay = 0.0;
+                        for (int h = 0; h < P; ++h) {
+                            ax += dk[(((size_t)t * 2 + 0) * P + h) * N + i] * S->psi[q * P + h];
+                            ay += dk[(((size_t)t * 2 + 1) * P + h) * N + i] * S->psi[q * P + h];
+                        }
+                        tk[(q * NTH + t) * 2 + 0] = ax;
+                        tk[(q * NTH + t) * 2 + 1] = ay;
+                    }
+                for (int q = 0; q < Q; ++q) {
+                    double k0x = kx[q], k0y = ky[q];
+                    /* the selected mechanism, as in collide_node */
+                    double target = u[1] * Gt, cum = 0.0;
+                    int l = 6;
+                    for (int m = 0; m < 6; ++m) { cum += g[q * 6 + m]; if (target < cum) { l = m; break; } }
+                    int changed = collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, &kx[q], &ky[q], &rej);
+                    if (changed) {
+                        double J[4];
+                        fs_jacobian(S, l, k0x, k0y, u[3], J);
+                        for (int t = 0; t < NTH; ++t) {
+                            double ax = tk[(q * NTH + t) * 2 + 0], ay = tk[(q * NTH + t) * 2 + 1];
+                            tk[(q * NTH + t) * 2 + 0] = J[0] * ax + J[1] * ay;
+                            tk[(q * NTH + t) * 2 + 1] = J[2] * ax + J[3] * ay;
+                        }
+                    }
+                }
+                project_particle(S, i, kx, ky);
+                for (int t = 0; t < NTH; ++t)
+                    for (int h = 0; h < P; ++h) {
+                        double ax = 0.0, ay = 0.0;
+                        for (int q = 0; q < Q; ++q) {
+                            double wp = S->wq[q] * S->psi[q * P + h];
+                            ax += wp * tk[(q * NTH + t) * 2 + 0];
+                            ay += wp * tk[(q * NTH + t) * 2 + 1];
+                        }
+                        dk[(((size_t)t * 2 + 0) * P + h) * N + i] = ax;
+                        dk[(((size_t)t * 2 + 1) * P + h) * N + i] = ay;
+                    }
+                recon_particle(S, i, kx, ky);
+                Gt = 0.0;
+                for (int q = 0; q < Q; ++q) {
+                    orc_rates_node(S, kx[q], ky[q], S->eps0q[q], &g[q * 6]);
+                    double sg = 0.0;
+                    for (int m = 0; m < 6; ++m) sg += g[q * 6 + m];
+                    if (sg > Gt) Gt = sg;
+                }
+                Gt *= (1.0 + c->alpha);
+                tc += dtc;
+                ++cc;
+                orc_draw(c, i, n, cc, u);
+                dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY;
+            }
+            free(tk);
+        }
+        S->step = n + 1;
+        S->n_out_of_grid = build_hist(S);
+        if (S->step % every == 0 && S->step > nsteps - window) {
+            tangent_observe(S, dk, Jq, dJq);
+            double m = 0.0, m2 = 0.0, dm[NTH] = {0, 0, 0, 0}, dm2[NTH] = {0, 0, 0, 0};
+            for (int q = 0; q < Q; ++q) {
+                m += S->wq[q] * Jq[q];
+                m2 += S->wq[q] * Jq[q] * Jq[q];
+                for (int t = 0; t < NTH; ++t) {
+                    dm[t] += S->wq[q] * dJq[q * NTH + t];
+                    dm2[t] += 2.0 * S->wq[q] * Jq[q] * dJq[q * NTH + t];
+                }
+            }
+            accJ += m;
+            accV += m2 - m * m;
+            for (int t = 0; t < NTH; ++t) { accdJ[t] += dm[t]; accdV[t] += dm2[t] - 2.0 * m * dm[t]; }
+            ++nout;
+        }
+    }
+    free(Jq); free(dJq); free(dk);
+    if (nout == 0) return -2;
+    val2[0] = accJ / nout;
+    val2[1] = accV / nout;
+    for (int t = 0; t < NTH; ++t) { grad8[t] = accdJ[t] / nout; grad8[NTH + t] = accdV[t] / nout; }
+    return 0;
+}
+
+/* Window averages of mean_z J_x and var_z J_x of an ordinary run (no tangents): the same
+ * objective as orc_tangent_run, for finite-difference checks. */
+int orc_window_objective(void *st, int64_t nsteps, int64_t every, int64_t window, double *val2)
+{
+    orc_state *S = (orc_state *)st;
+    double accJ = 0.0, accV = 0.0;
+    int64_t nout = 0;
+    int64_t s0 = S->step;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        step_once(S);
+        if ((S->step - s0) % every == 0 && (S->step - s0) > nsteps - window) {
+            record_moments(S);
+            accJ += S->mean[(S->T_out - 1) * 4 + 3];
+            accV += S->var[(S->T_out - 1) * 4 + 3];
+            ++nout;
+        }
+    }
+    if (nout == 0) return -2;
+    val2[0] = accJ / nout;
+    val2[1] = accV / nout;
+    return 0;
 }

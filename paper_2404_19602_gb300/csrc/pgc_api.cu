@@ -195,6 +195,8 @@ static void build_tables(const pgc_config &c, HostTables &t)
                 }
     }
     const bool er = c.eps0_eV.lo != c.eps0_eV.hi, fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
+    t.eps_random = er;
+    t.field_random = fr;
     t.psi.assign((size_t)Q * P, 0.0);
     t.wpsi.assign((size_t)Q * P, 0.0);
     t.eps0.assign(Q, 0.0); t.Ex.assign(Q, 0.0); t.dq.assign(Q, 0.0); t.nq.assign(Q, 0.0);
@@ -565,6 +567,7 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     } else {
         if ((e = ctx->run->init_sample(s)) != cudaSuccess) st = cuda_fail(ctx, e, "init kernel");
         else st = observe_current(ctx, true, true);
+        ctx->sampled = true;
     }
     if (st != PGC_OK) {
         std::string m = ctx->err;
@@ -690,6 +693,7 @@ pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
             else ((float *)tmp)[(size_t)p * ld + i] = 0.0f;
         }
     }
+    ctx->sampled = false;
     e = cudaMemcpyAsync(ctx->b.state, tmp, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");

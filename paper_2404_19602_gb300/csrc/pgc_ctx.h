@@ -21,6 +21,7 @@ struct pgc_ctx {
     double *series = nullptr;
     uint32_t *tmp_max = nullptr;
     bool failed = false;
+    bool sampled = false;  // state comes from the initial Fermi-Dirac sampling (no upload since)
     std::string err;
     // kernel timing samples (pgc_profile): events around phase 1 / phase 2 of sampled steps
     int prof_every = 0;

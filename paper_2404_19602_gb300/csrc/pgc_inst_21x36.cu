@@ -1,4 +1,5 @@
 // Kernels for the basis size P = 21 and 36 quadrature node(s), FP32 and FP64.
+#include "pgc_adjoint.cuh"
 #include "pgc_batch.cuh"
 
 namespace pgc {
@@ -12,4 +13,9 @@ BatchRunner *make_batch_runner_21x36(int precision, const std::vector<BatchCase>
     return make_batch_runner_shape<21, 36>(precision, cases, sc, num_sms);
 }
 size_t case_dev_size_21x36(int precision) { return case_dev_bytes<21, 36>(precision); }
+AdjRunner *make_adj_runner_21x36(int precision, const HostTables &t, const DevBuffers &b, const AdjBuffers &ab,
+                                int num_sms)
+{
+    return make_adj_runner_shape<21, 36>(precision, t, b, ab, num_sms);
+}
 }  // namespace pgc

@@ -12,6 +12,7 @@ namespace pgc {
 // Every FP64 table a context needs, built on the host (pgc_tables.cpp).
 struct HostTables {
     int d = 0, P = 1, Q = 1;
+    bool eps_random = false, field_random = false;
     std::vector<double> z;      // [Q][d] nodes in [-1,1]^d
     std::vector<double> w;      // [Q]
     std::vector<double> psi;    // [Q][P]
@@ -78,6 +79,11 @@ class BatchRunner;
 BatchRunner *make_batch_runner(int P, int Q, int precision, const std::vector<BatchCase> &cases,
                                const BatchScratch &sc, int num_sms);
 size_t case_dev_size(int P, int Q, int precision);
+
+struct AdjBuffers;
+class AdjRunner;
+AdjRunner *make_adj_runner(int P, int Q, int precision, const HostTables &t, const DevBuffers &b, const AdjBuffers &ab,
+                           int num_sms);
 
 // Launch accounting (every kernel launch of the library increments it).
 void count_launch(uint64_t n = 1);

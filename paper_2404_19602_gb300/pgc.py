@@ -77,6 +77,8 @@ SIGNATURES = {
     "pgc_batch_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _dp]),
     "pgc_batch_destroy": (None, [_vp]),
     "pgc_batch_last_error": (C.c_char_p, [_vp]),
+    "pgc_adjoint_query_sizes": (C.c_int, [_vp, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]),
+    "pgc_adjoint": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, _dp, _vp, _dp, _dp]),
     "pgc_destroy": (None, [_vp]),
     "pgc_last_error": (C.c_char_p, [_vp]),
     "pgc_status_string": (C.c_char_p, [C.c_int]),
@@ -237,6 +239,23 @@ def pgc_batch_destroy(b):
         lib().pgc_batch_destroy(_vp(b))
 
 
+def pgc_adjoint_query_sizes(ctx, n_steps: int, ckpt_every: int) -> int:
+    n = C.c_size_t()
+    _check(lib().pgc_adjoint_query_sizes(_vp(ctx), int(n_steps), int(ckpt_every), C.byref(n)), _vp(ctx))
+    return n.value
+
+
+def pgc_adjoint(ctx, n_steps: int, ckpt_every: int, moments_every: int, window_steps: int, weights, d_work: int):
+    """Returns (value[2] = (Jbar, Vbar), grad[4] = dL/d(E_lo, E_hi, eps0_lo, eps0_hi)) for
+    L = weights[0] Jbar + weights[1] Vbar; see include/pgc.h."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    val = np.zeros(2)
+    grad = np.zeros(4)
+    _check(lib().pgc_adjoint(_vp(ctx), int(n_steps), int(ckpt_every), int(moments_every), int(window_steps),
+                             _ptr(w, _dp), _vp(d_work), _ptr(val, _dp), _ptr(grad, _dp)), _vp(ctx))
+    return val, grad
+
+
 def pgc_destroy(ctx):
     if ctx:
         lib().pgc_destroy(_vp(ctx))
@@ -373,4 +392,59 @@ class BatchSimulation:
             self.close()
         except Exception:
             pass
+
+
+def window_objective(params: dict, n_steps: int, moments_every: int, window_steps: int):
+    """(Jbar, Vbar): averages over the moment records in (n_steps - window_steps, n_steps] of the
+    mean and the variance over z of the current J_x, from a plain run."""
+    sim = Simulation(params, max_outputs=n_steps // moments_every + 2)
+    sim.step(n_steps, moments_every)
+    m = sim.moments()
+    sim.close()
+    n = np.rint(m["t_fs"] / params["dt_fs"]).astype(np.int64)
+    sel = (n > n_steps - window_steps) & (n <= n_steps)
+    return float(m["mean"][sel, 3].mean()), float(m["var"][sel, 3].mean())
+
+
+def adjoint(params: dict, n_steps: int, ckpt_every: int, moments_every: int, window_steps: int, weights=(1.0, 0.0)):
+    """Pathwise gradient by the hand-written adjoint kernels (see pgc_adjoint in include/pgc.h)."""
+    import torch
+
+    sim = Simulation(params, max_outputs=n_steps // moments_every + 2)
+    nbytes = pgc_adjoint_query_sizes(sim.ctx, n_steps, ckpt_every)
+    work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=sim.state_buf.device)
+    val, grad = pgc_adjoint(sim.ctx, n_steps, ckpt_every, moments_every, window_steps, weights, work.data_ptr())
+    sim.close()
+    return val, grad
+
+
+def _torch_function():
+    import torch
+
+    class SteadyCurrent(torch.autograd.Function):
+        """(Jbar, Vbar) of a run as a differentiable function of theta = (E_lo, E_hi, eps0_lo, eps0_hi)
+        (V/cm, V/cm, eV, eV).  forward: a plain run; backward: the adjoint (events frozen, states
+        checkpointed every ckpt_every steps and recomputed)."""
+
+        @staticmethod
+        def forward(fctx, theta, params, n_steps, moments_every, window_steps, ckpt_every):
+            th = theta.detach().to("cpu", torch.float64).numpy()
+            p = dict(params, Ex_lo=float(th[0]), Ex_hi=float(th[1]), eps0_lo=float(th[2]), eps0_hi=float(th[3]))
+            fctx.cfg = (p, n_steps, moments_every, window_steps, ckpt_every)
+            J, V = window_objective(p, n_steps, moments_every, window_steps)
+            return torch.tensor([J, V], dtype=torch.float64, device=theta.device)
+
+        @staticmethod
+        def backward(fctx, grad_out):
+            p, n_steps, every, window, ckpt = fctx.cfg
+            g = grad_out.detach().to("cpu", torch.float64).numpy()
+            _, grad = adjoint(p, n_steps, ckpt, every, window, weights=g)
+            return torch.tensor(grad, dtype=torch.float64), None, None, None, None, None
+
+    return SteadyCurrent
+
+
+def steady_current(theta, params: dict, n_steps: int, moments_every: int, window_steps: int, ckpt_every: int = 250):
+    """Differentiable (Jbar, Vbar); see SteadyCurrent."""
+    return _torch_function().apply(theta, params, n_steps, moments_every, window_steps, ckpt_every)
 
