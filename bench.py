@@ -32,7 +32,8 @@ if ROOT not in sys.path:
 
 from paper_2404_19602_gb300 import workloads as W  # noqa: E402
 
-WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None}
+WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None,
+             "adjoint": W.ADJOINT_1E6}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -47,7 +48,10 @@ def parse():
     ap.add_argument("--impl", default="pgc", choices=["pgc", "reference"])
     ap.add_argument("--workload", default="gap_uq", choices=sorted(WORKLOADS),
                     help="gap_uq (1e6 particles, 1 random input), det (1e4, FP64), gap_field (4e6, 2 random "
-                         "inputs), sweep (64 cases in one batched CUDA-graph sequence)")
+                         "inputs), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
+                         "reverse sweep of the steady-current sensitivities, 1e6 particles)")
+    ap.add_argument("--fd-check", action="store_true",
+                    help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
     ap.add_argument("--moments-every", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
@@ -243,6 +247,72 @@ def run_sweep(args, pgc, torch, dev, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, pgc, torch, dev, rank, world):
+    """One step = a full adjoint evaluation: forward --time-steps steps with checkpoints every 250,
+    then the reverse sweep (segment replay + backward kernels) of the window-averaged mean and
+    variance of J_x over the last 250 steps; the metric counts forward particle-steps."""
+    p = W.scaled(WORKLOADS["adjoint"], stream_id=rank)
+    S, K = args.time_steps, args.steps
+    every, window, ckpt = args.moments_every, min(p["steady_window"], S), p["ckpt_every"]
+    sims = []
+
+    def one():
+        sim = pgc.Simulation(p, max_outputs=S // every + 2)
+        nbytes = pgc.pgc_adjoint_query_sizes(sim.ctx, S, ckpt)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        val, grad = pgc.pgc_adjoint(sim.ctx, S, ckpt, every, window, [1.0, 0.0], work.data_ptr())
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        sim.close()
+        return e0.elapsed_time(e1), val, grad, nbytes
+
+    for _ in range(args.warmup):
+        one()
+    launches0 = pgc.pgc_launch_count()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    res = [one() for _ in range(K)]
+    clk = clocks.stop()
+    launches = pgc.pgc_launch_count() - launches0
+    ms = sum(r[0] for r in res)
+    val, grad, nbytes = res[-1][1], res[-1][2], res[-1][3]
+    fd = None
+    if args.fd_check:
+        keys = ["Ex_lo", "Ex_hi", "eps0_lo", "eps0_hi"]
+        fd = []
+        for t, key in enumerate(keys):
+            pair = ("Ex_lo", "Ex_hi") if t < 2 else ("eps0_lo", "eps0_hi")
+            h = 1e-3 * abs(p[key])
+            vals = []
+            for sgn in (1, -1):
+                q = dict(p)
+                if p[pair[0]] == p[pair[1]]:
+                    q[pair[0]] += sgn * h
+                    q[pair[1]] += sgn * h
+                else:
+                    q[key] += sgn * h
+                vals.append(pgc.window_objective(q, S, every, window)[0])
+            f = 2.0 if p[pair[0]] == p[pair[1]] else 1.0
+            fd.append((vals[0] - vals[1]) / (2 * h) / f)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": p["N"] * world * S * K / (ms / 1e3), "unit": METRIC, "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": p["name"], "particles_per_gpu": p["N"], "time_steps": S, "ckpt_every": ckpt,
+                       "window_steps": window, "moments_every": every, "work_bytes": nbytes,
+                       "note": "one step = forward with checkpoints + reverse sweep; metric counts forward particle-steps"},
+            "adjoint": {"Jbar_A_per_m": val[0], "VarJ": val[1],
+                        "dJbar_d(E_lo,E_hi,eps0_lo,eps0_hi)": list(grad),
+                        "central_fd_h1e-3_crn": fd},
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": None, "e2e": None, "roofline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -266,8 +336,8 @@ def main():
     from paper_2404_19602_gb300 import build as B
 
     B.build()
-    if args.workload == "sweep":
-        run_sweep(args, pgc, torch, dev, rank, world)
+    if args.workload in ("sweep", "adjoint"):
+        (run_sweep if args.workload == "sweep" else run_adjoint)(args, pgc, torch, dev, rank, world)
         if world > 1:
             dist.destroy_process_group()
         return

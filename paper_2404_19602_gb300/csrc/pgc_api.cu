@@ -594,7 +594,7 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
     f.vF_ms = ctx->t.vF_ms;
     f.Q = ctx->t.Q;
     f.g1 = ctx->run->grid1();
-    f.g2 = kGrid2;
+    f.g2 = ctx->run->grid2();
     for (int64_t k = 0; k < n_steps; ++k) {
         const int64_t n = ctx->step;
         const bool out = moments_every > 0 && ((n + 1) % moments_every == 0);

@@ -217,40 +217,46 @@ __device__ __forceinline__ R rate_bound(const Phys<R> &ph, R eps, R eps0max)
 template <typename R>
 __device__ R solve_angle(R u, R sgn)
 {
-    const R t = (R)(2.0 * kPi) * u;
-    R lo = (R)0, hi = (R)(2.0 * kPi);
-    const int iters = (sizeof(R) == 8) ? 60 : 28;
+    // f(th) = th + sgn sin th - 2 pi u is non-decreasing on [0, 2pi]; safeguarded Newton from a
+    // start that captures the cubic behaviour at the stationary point (th = pi for sgn = +1,
+    // th = 0 or 2pi for sgn = -1).
+    const R twopi = (R)(2.0 * kPi), t = twopi * u;
+    R lo = (R)0, hi = twopi, th;
+    if (sgn > (R)0) th = (R)kPi + cbrt((R)6 * (t - (R)kPi));
+    else th = (t < (R)kPi) ? cbrt((R)6 * t) : twopi - cbrt((R)6 * (twopi - t));
+    th = fmin(fmax(th, (R)0), twopi);
+    const int iters = (sizeof(R) == 8) ? 60 : 30;
+    const R tol = (sizeof(R) == 8) ? (R)1e-15 : (R)2e-7;
     for (int it = 0; it < iters; ++it) {
-        const R mid = (R)0.5 * (lo + hi);
-        if (mid + sgn * rsin<R>(mid) < t) lo = mid; else hi = mid;
+        R s, c;
+        rsincos<R>(th, &s, &c);
+        const R f = th + sgn * s - t, df = (R)1 + sgn * c;
+        if (f < (R)0) lo = th; else hi = th;
+        R tn = (df > (R)0) ? th - f / df : (R)0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = (R)0.5 * (lo + hi);
+        const R d = fabs(tn - th);
+        th = tn;
+        if (d <= tol * twopi || hi - lo <= tol * twopi) break;
     }
-    return (R)0.5 * (lo + hi);
+    return th;
 }
 
 // Edge final angle: absolute angle with density exp(-beta (c - cos th')^2), inverted through
-// the trapezoid CDF on the n_theta grid, linear between grid points.
+// the trapezoid CDF on the n_theta grid, linear between grid points.  The total of the CDF is
+// T(beta, c) (edge_T); one pass up to the target's segment.
 template <typename R>
 __device__ R edge_angle(const Phys<R> &ph, R beta, R c, R u)
 {
     const int n = ph.n_theta;
-    // total first (the grid values are cheap to recompute)
-    R prev = rexp<R>(-beta * (ph.cosj[0] - c) * (ph.cosj[0] - c));
-    R total = (R)0;
-    for (int j = 1; j <= n; ++j) {
-        const R x = ph.cosj[j] - c;
-        const R g = rexp<R>(-beta * x * x);
-        total += (R)0.5 * ph.edge_h * (prev + g);
-        prev = g;
-    }
-    const R target = u * total;
+    const R target = u * edge_T<R>(ph, beta, c);
     R C = (R)0;
-    prev = rexp<R>(-beta * (ph.cosj[0] - c) * (ph.cosj[0] - c));
+    R prev = rexp<R>(-beta * (ph.cosj[0] - c) * (ph.cosj[0] - c));
     for (int j = 1; j <= n; ++j) {
         const R x = ph.cosj[j] - c;
         const R g = rexp<R>(-beta * x * x);
         const R Cn = C + (R)0.5 * ph.edge_h * (prev + g);
         if (Cn > target || j == n) {
-            const R frac = (target - C) / (Cn - C);
+            const R frac = fmin(fmax((target - C) / (Cn - C), (R)0), (R)1);
             return ((R)(j - 1) + frac) * ph.edge_h;
         }
         C = Cn;

@@ -440,15 +440,13 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         const int q = r + s * G;
         if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
     }
+    R gc[NPL][6];  // rates of the current state at the lane's nodes (reused by the selection)
     auto majorant = [&]() {
         R gm = (R)0;
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
-            if (q < Q) {
-                R g[6];
-                gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], g));
-            }
+            if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
         }
         return ph.alpha1 * group_max<G>(gm, gmask);
     };
@@ -470,13 +468,11 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
             if (q >= Q) continue;
-            R g[6];
-            rates6(ph, kx[s], ky[s], nd.eps0[q], g);
             int l = 6;
             R cum = (R)0;
 #pragma unroll
             for (int m = 0; m < 6; ++m) {
-                cum += g[m];
+                cum += gc[s][m];
                 if (l == 6 && target < cum) l = m;
             }
             if (l == 6) continue;  // self scattering: h^7 = identity
@@ -553,7 +549,7 @@ __device__ __forceinline__ void stage(uint32_t *dst, const T &src)
 }
 
 template <int P, int Q, typename R>
-__global__ void __launch_bounds__(kPhase2Threads)
+__global__ void __launch_bounds__(kPhase2Threads, 4)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
     constexpr int G = GroupOf<Q>::G;

@@ -52,6 +52,7 @@ class Runner {
 public:
     virtual ~Runner() {}
     virtual int grid1() const = 0;
+    virtual int grid2() const = 0;
     // sample the Fermi-Dirac initial state into the state buffer
     virtual cudaError_t init_sample(cudaStream_t s) = 0;
     // histogram of the current state into hist buffer `buf` and moment partials into part1

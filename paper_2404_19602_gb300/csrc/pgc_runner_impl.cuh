@@ -68,9 +68,14 @@ public:
         if (per_block >= 65535) win = false;
         args_.use_win = win ? 1 : 0;
         if (!win) win_bytes_ = 0;
+        // phase 2: one resident wave (its work is one latency-bound collision chain per group)
+        int per_sm2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_phase2<P, Q, R>, kPhase2Threads, 0);
+        grid2_ = std::max(1, std::min(kGrid2, num_sms * std::max(per_sm2, 1)));
     }
 
     int grid1() const override { return grid1_; }
+    int grid2() const override { return grid2_; }
     const StepArgs<P, Q, R> &args() const { return args_; }
 
     cudaError_t init_sample(cudaStream_t s) override
@@ -116,7 +121,7 @@ public:
         if (ev) cudaEventRecord(ev[0], s);
         k_phase1<P, Q, R><<<grid1_, kPhase1Threads, win_bytes_, s>>>(a);
         if (ev) cudaEventRecord(ev[1], s);
-        k_phase2<P, Q, R><<<kGrid2, kPhase2Threads, 0, s>>>(a);
+        k_phase2<P, Q, R><<<grid2_, kPhase2Threads, 0, s>>>(a);
         if (ev) cudaEventRecord(ev[2], s);
         count_launch(2);
         return cudaGetLastError();
@@ -183,6 +188,7 @@ private:
     InitArgs<P, Q> init_{};
     int grid1_ = 1;
     size_t win_bytes_ = 0;
+    int grid2_ = 1;
 };
 
 template <int P, int Q>
