@@ -93,7 +93,7 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
                 ly[h] = a.lam[(int64_t)(P + h) * a.ld + i];
             }
             if (a.inject) {
-                // dL/dk(z_q) = dL/dJ_q cJ n_q d vhat/dk,  vhat = hvF kx / eps(k, eps0_q)
+                // dL/dk(z_q) = dL/dJ_q cJ n_q d vhat/dk,  vhat = hvF kx / eps(k, eps0_q)  (in R)
                 R cx[P], cy[P];
 #pragma unroll
                 for (int h = 0; h < P; ++h) {
@@ -104,23 +104,23 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
                 for (int q = 0; q < Q; ++q) {
                     R kx, ky;
                     recon_node(nd, q, cx, cy, kx, ky);
-                    const double e0 = (double)nd.eps0[q];
-                    const double hv = (double)ph.hvF;
-                    const double eps = sqrt(hv * hv * ((double)kx * kx + (double)ky * ky) + e0 * e0);
-                    const double e3 = eps * eps * eps;
-                    const double vhat = hv * kx / eps;
-                    const double dvx = hv / eps - hv * hv * hv * (double)kx * kx / e3;
-                    const double dvy = -hv * hv * hv * (double)kx * ky / e3;
-                    const double dve = -hv * (double)kx * e0 / e3;
+                    const R e0 = nd.eps0[q], hv = ph.hvF;
+                    const R eps = rsqrt_<R>(ph.hvF2 * (kx * kx + ky * ky) + e0 * e0);
+                    const R ie = (R)1 / eps, ie3 = ie * ie * ie;
+                    const R vhat = hv * kx * ie;
+                    const R dvx = hv * ie - hv * ph.hvF2 * kx * kx * ie3;
+                    const R dvy = -hv * ph.hvF2 * kx * ky * ie3;
+                    const R dve = -hv * kx * e0 * ie3;
                     const double s = a.dLdJ[q] * a.cJ;
-                    const R gx = (R)(s * a.nq[q] * dvx), gy = (R)(s * a.nq[q] * dvy);
+                    const R gx = (R)(s * a.nq[q]) * dvx, gy = (R)(s * a.nq[q]) * dvy;
 #pragma unroll
                     for (int h = 0; h < P; ++h) {
                         lx[h] += gx * nd.psi[q * P + h];
                         ly[h] += gy * nd.psi[q * P + h];
                     }
 #pragma unroll
-                    for (int t = 0; t < NTH; ++t) g[t] += s * (a.dnq[q] * a.de0[q][t] * vhat + a.nq[q] * dve * a.de0[q][t]);
+                    for (int t = 0; t < NTH; ++t)
+                        g[t] += s * (a.dnq[q] * a.de0[q][t] * (double)vhat + a.nq[q] * (double)dve * a.de0[q][t]);
                 }
 #pragma unroll
                 for (int h = 0; h < P; ++h) {

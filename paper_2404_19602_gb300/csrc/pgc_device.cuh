@@ -405,15 +405,19 @@ __host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, 
             const double mid = 0.5 * (lo + hi);
             if (resid(mid) < 0.0) lo = mid; else hi = mid;
         }
+    // Newton from the bracket midpoint; quadratic convergence from the FP32 bracket reaches
+    // rounding level in 2-3 steps, so stop once a step is below a few ulps (Newton iterates can
+    // oscillate by an ulp and never meet a tighter test).
     double e = 0.5 * (lo + hi);
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < 12; ++it) {
         const double r = resid(e);
         if (r < 0.0) lo = e; else hi = e;
         const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
         double en = (dens > 0.0) ? e - r / dens : 0.5 * (lo + hi);
         if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
-        if (fabs(en - e) <= 2e-16 * e || hi - lo <= 4e-16 * hi) { e = en; break; }
+        const double step = fabs(en - e);
         e = en;
+        if (step <= 8e-16 * e) break;
     }
     return e;
 }

@@ -488,7 +488,7 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         }
         if (group_any<G>(changed, gmask) && r == 0) ++cnt.chg;
         // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
-#pragma unroll
+#pragma unroll (P * Q <= 64 ? P : 1)
         for (int h = 0; h < P; ++h) {
             R sx = (R)0, sy = (R)0;
 #pragma unroll
