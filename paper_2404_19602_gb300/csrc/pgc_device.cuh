@@ -101,35 +101,23 @@ template <> __device__ __forceinline__ double rfloor<double>(double x) { return 
 template <typename R>
 __device__ __forceinline__ bool cell_rl(const Phys<R> &ph, R kx, R ky, int &r, int &l)
 {
-    R fr, fl;
+    // floor and conversion in one rounding-down conversion; outside the grid (including the
+    // saturated conversions of huge values) fails the unsigned comparison
     if constexpr (sizeof(R) == 8) {
-        fr = floor((kx + ph.Lk) / ph.dk);
-        fl = floor((ky + ph.Lk) / ph.dk);
+        r = __double2int_rd((kx + ph.Lk) / ph.dk);
+        l = __double2int_rd((ky + ph.Lk) / ph.dk);
     } else {
-        fr = floorf((kx + ph.Lk) * ph.inv_dk);
-        fl = floorf((ky + ph.Lk) * ph.inv_dk);
+        r = __float2int_rd((kx + ph.Lk) * ph.inv_dk);
+        l = __float2int_rd((ky + ph.Lk) * ph.inv_dk);
     }
-    const R nk = (R)ph.Nk;
-    if (!(fr >= (R)0) || !(fl >= (R)0) || fr >= nk || fl >= nk) return false;
-    r = (int)fr;
-    l = (int)fl;
-    return true;
+    return (unsigned)r < (unsigned)ph.Nk && (unsigned)l < (unsigned)ph.Nk;
 }
 
 template <typename R>
 __device__ __forceinline__ int cell_of(const Phys<R> &ph, R kx, R ky)
 {
-    R fr, fl;
-    if constexpr (sizeof(R) == 8) {
-        fr = floor((kx + ph.Lk) / ph.dk);
-        fl = floor((ky + ph.Lk) / ph.dk);
-    } else {
-        fr = floorf((kx + ph.Lk) * ph.inv_dk);
-        fl = floorf((ky + ph.Lk) * ph.inv_dk);
-    }
-    const R nk = (R)ph.Nk;
-    if (!(fr >= (R)0) || !(fl >= (R)0) || fr >= nk || fl >= nk) return -1;
-    return (int)fr * ph.Nk + (int)fl;
+    int r, l;
+    return cell_rl(ph, kx, ky, r, l) ? r * ph.Nk + l : -1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -231,9 +219,10 @@ __device__ R solve_angle(R u, R sgn)
         R s, c;
         rsincos<R>(th, &s, &c);
         const R f = th + sgn * s - t, df = (R)1 + sgn * c;
+        if (f == (R)0) break;  // exact root
         if (f < (R)0) lo = th; else hi = th;
         R tn = (df > (R)0) ? th - f / df : (R)0.5 * (lo + hi);
-        if (!(tn > lo && tn < hi)) tn = (R)0.5 * (lo + hi);
+        if (!(tn >= lo && tn <= hi)) tn = (R)0.5 * (lo + hi);  // keep the iterate in the bracket
         const R d = fabs(tn - th);
         th = tn;
         if (d <= tol * twopi || hi - lo <= tol * twopi) break;
@@ -409,15 +398,16 @@ __host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, 
     // rounding level in 2-3 steps, so stop once a step is below a few ulps (Newton iterates can
     // oscillate by an ulp and never meet a tighter test).
     double e = 0.5 * (lo + hi);
-    for (int it = 0; it < 12; ++it) {
+    for (int it = 0; it < 16; ++it) {
         const double r = resid(e);
+        if (r == 0.0) break;  // exact root
         if (r < 0.0) lo = e; else hi = e;
         const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
         double en = (dens > 0.0) ? e - r / dens : 0.5 * (lo + hi);
-        if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
+        if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);  // keep the iterate in the bracket
         const double step = fabs(en - e);
         e = en;
-        if (step <= 8e-16 * e) break;
+        if (step <= 4e-16 * e) break;
     }
     return e;
 }
