@@ -139,6 +139,28 @@ def _traffic(kernel: str, workload: str):
         return None
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Maximum of a per-rank number over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(p: dict, rank: int) -> dict:
+    """The ensemble a rank advances: the same workload on its own Philox stream."""
+    return W.scaled(p, stream_id=p.get("stream_id", 0) + rank)
+
+
+def throughput(n_particles: int, world: int, time_steps: int, steps: int, ms: float) -> float:
+    """Whole-job particle-steps/s: every rank advances n_particles for time_steps x steps."""
+    return n_particles * world * time_steps * steps / (ms / 1e3)
+
+
 def cpu_baseline(p):
     """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
     import oracle as O
@@ -221,12 +243,8 @@ def run_sweep(args, pgc, torch, dev, rank, world):
         dist.barrier()
     launches = pgc.pgc_launch_count() - launches0
     clk = clocks.stop()
-    gpu_ms = sum(x.elapsed_time(y) for x, y in ev)
-    t = torch.tensor([gpu_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    gpu_ms = float(t.item())
-    value = ntot * world * S * K / (gpu_ms / 1e3)
+    gpu_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), dev)
+    value = throughput(ntot, world, S, K, gpu_ms)
     peak, peak_kind = _peaks()
     by = ntot * (2 * 6 * 4 + 4)
     achieved = by / (gpu_ms / K / S / 1e3) / 1e9
@@ -251,7 +269,7 @@ def run_adjoint(args, pgc, torch, dev, rank, world):
     """One step = a full adjoint evaluation: forward --time-steps steps with checkpoints every 250,
     then the reverse sweep (segment replay + backward kernels) of the window-averaged mean and
     variance of J_x over the last 250 steps; the metric counts forward particle-steps."""
-    p = W.scaled(WORKLOADS["adjoint"], stream_id=rank)
+    p = rank_workload(WORKLOADS["adjoint"], rank)
     S, K = args.time_steps, args.steps
     every, window, ckpt = args.moments_every, min(p["steady_window"], S), p["ckpt_every"]
     sims = []
@@ -341,7 +359,7 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    p = W.scaled(WORKLOADS[args.workload], stream_id=rank)
+    p = rank_workload(WORKLOADS[args.workload], rank)
     S, K = args.time_steps, args.steps
     every = args.moments_every
     cap = (K + args.warmup) * S // max(every, 1) + 8
@@ -381,12 +399,9 @@ def main():
     gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
     prof = pgc.pgc_profile_read(sim.ctx)
     cnt = sim.counters()
-    t = torch.tensor([gpu_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    gpu_ms_max = float(t.item())
+    gpu_ms_max = max_over_ranks(gpu_ms, dev)
     N = p["N"]
-    value = N * world * S * K / (gpu_ms_max / 1e3)
+    value = throughput(N, world, S, K, gpu_ms_max)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     P, Q = sim.P, sim.Q
@@ -419,12 +434,9 @@ def main():
             sim2.step(S, every)
             m = sim2.moments()                       # D2H of the moment series (synchronizes)
         barrier()
-        e_dt = time.perf_counter() - e0
-        te = torch.tensor([e_dt], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e_dt = max_over_ranks(time.perf_counter() - e0, dev)
         state_bytes = pgc.pgc_query_sizes(sim2.cfg)["state_bytes"]
-        e2e = {"value": N * world * S * K / float(te.item()), "unit": METRIC,
+        e2e = {"value": throughput(N, world, S, K, e_dt * 1e3), "unit": METRIC,
                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": int(m["t_fs"].size * (1 + 4 * Q + 8) * 8)}
         sim2.close()
     else:

@@ -110,6 +110,9 @@ def lib():
             L.orc_tangent_run.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, dp, dp]
             L.orc_window_objective.restype = C.c_int
             L.orc_window_objective.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, dp]
+            L.orc_step_particles.argtypes = [vp, i64p, C.c_int64]
+            L.orc_set_step.argtypes = [vp, C.c_int64]
+            L.orc_set_nmax.argtypes = [vp, u32p]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -322,6 +325,19 @@ class Oracle:
         if r != 0:
             raise RuntimeError("orc_window_objective failed (%d)" % r)
         return val
+
+    def step_particles(self, idx):
+        """Advance only the particles idx by one time step against the current histogram
+        (test hook; the step counter and the histogram stay)."""
+        a = np.ascontiguousarray(idx, dtype=np.int64)
+        lib().orc_step_particles(self._h, a.ctypes.data_as(C.POINTER(C.c_int64)), a.size)
+
+    def set_step(self, step):
+        lib().orc_set_step(self._h, int(step))
+
+    def set_nmax(self, nmax):
+        a = np.ascontiguousarray(nmax, dtype=np.uint32)
+        lib().orc_set_nmax(self._h, _u32p(a))
 
     def observe_at(self, z):
         z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.float64)

@@ -792,26 +792,43 @@ static int collide_node(const orc_state *S, int q, double Gt, const double *g, d
 /* again from the current state (standard DSMC; a single draw per step would give an         */
 /* unbounded number of collisions, since E[1/dt] diverges for exponential dt).                */
 /* ------------------------------------------------------------------------------------------ */
-static void step_once(orc_state *S)
+/* One time step of particle i (drift, then the collision loop) against f^n = Hn. */
+static void step_particle(orc_state *S, int64_t i, int64_t n, const uint32_t *Hn, const uint32_t *Nmx,
+                          int64_t *att_, int64_t *real_, int64_t *rej_, int64_t *cap_)
 {
     const orc_cfg *c = &S->cfg;
     int P = S->P, Q = S->Q;
     int64_t N = c->N;
-    int64_t n = S->step;
-    const uint32_t *Hn = S->H;
-    uint32_t Nmx[1296];
-    if (c->pauli_norm == ORC_PAULI_CURRENT_MAX) hist_max(S, Nmx);
-    else memcpy(Nmx, S->Nmax, sizeof(uint32_t) * Q);
+    double kx[1296], ky[1296], g[1296 * 6];
     int64_t att = 0, real = 0, rej = 0, cap = 0;
-
-#pragma omp parallel for schedule(dynamic, 256) reduction(+ : att, real, rej, cap)
-    for (int64_t i = 0; i < N; ++i) {
-        double kx[1296], ky[1296], g[1296 * 6];
-        /* drift of the coefficients */
-        for (int h = 0; h < P; ++h) S->khat[((size_t)0 * P + h) * N + i] -= S->dhat[h];
+    /* drift of the coefficients */
+    for (int h = 0; h < P; ++h) S->khat[((size_t)0 * P + h) * N + i] -= S->dhat[h];
+    recon_particle(S, i, kx, ky);
+    /* majorant: Gt = (1+alpha) max_q sum_nu Gamma_nu(k(z_q))  (Eq. (19), Eq. (25)) */
+    double Gt = 0.0;
+    for (int q = 0; q < Q; ++q) {
+        orc_rates_node(S, kx[q], ky[q], S->eps0q[q], &g[q * 6]);
+        double sg = 0.0;
+        for (int m = 0; m < 6; ++m) sg += g[q * 6 + m];
+        if (sg > Gt) Gt = sg;
+    }
+    Gt *= (1.0 + c->alpha);
+    double tc = 0.0;
+    uint32_t cc = 0;
+    double u[4];
+    orc_draw(c, i, n, cc, u);
+    double dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY; /* Eq. (18) / (25) */
+    while (tc + dtc < c->dt_fs) {
+        if ((int)cc >= c->max_coll) { ++cap; break; }
+        ++att;
+        int changed = 0;
+        for (int q = 0; q < Q; ++q)
+            changed |= collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, &kx[q], &ky[q], &rej);
+        if (changed) ++real;
+        /* collisional matrices K1 + K2 (Eqs. (28)-(30)): project the per-node result */
+        project_particle(S, i, kx, ky);
         recon_particle(S, i, kx, ky);
-        /* majorant: Gt = (1+alpha) max_q sum_nu Gamma_nu(k(z_q))  (Eq. (19), Eq. (25)) */
-        double Gt = 0.0;
+        Gt = 0.0;
         for (int q = 0; q < Q; ++q) {
             orc_rates_node(S, kx[q], ky[q], S->eps0q[q], &g[q * 6]);
             double sg = 0.0;
@@ -819,38 +836,27 @@ static void step_once(orc_state *S)
             if (sg > Gt) Gt = sg;
         }
         Gt *= (1.0 + c->alpha);
-        double tc = 0.0;
-        uint32_t cc = 0;
-        double u[4];
+        tc += dtc;
+        ++cc;
         orc_draw(c, i, n, cc, u);
-        double dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY; /* Eq. (18) / (25) */
-        while (tc + dtc < c->dt_fs) {
-            if ((int)cc >= c->max_coll) { ++cap; break; }
-            ++att;
-            int changed = 0;
-            for (int q = 0; q < Q; ++q) {
-                int64_t r0 = rej;
-                changed |= collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, &kx[q], &ky[q], &rej);
-                (void)r0;
-            }
-            if (changed) ++real;
-            /* collisional matrices K1 + K2 (Eqs. (28)-(30)): project the per-node result */
-            project_particle(S, i, kx, ky);
-            recon_particle(S, i, kx, ky);
-            Gt = 0.0;
-            for (int q = 0; q < Q; ++q) {
-                orc_rates_node(S, kx[q], ky[q], S->eps0q[q], &g[q * 6]);
-                double sg = 0.0;
-                for (int m = 0; m < 6; ++m) sg += g[q * 6 + m];
-                if (sg > Gt) Gt = sg;
-            }
-            Gt *= (1.0 + c->alpha);
-            tc += dtc;
-            ++cc;
-            orc_draw(c, i, n, cc, u);
-            dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY;
-        }
+        dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY;
     }
+    *att_ += att; *real_ += real; *rej_ += rej; *cap_ += cap;
+}
+
+static void step_once(orc_state *S)
+{
+    const orc_cfg *c = &S->cfg;
+    int Q = S->Q;
+    int64_t N = c->N;
+    int64_t n = S->step;
+    const uint32_t *Hn = S->H;
+    uint32_t Nmx[1296];
+    if (c->pauli_norm == ORC_PAULI_CURRENT_MAX) hist_max(S, Nmx);
+    else memcpy(Nmx, S->Nmax, sizeof(uint32_t) * Q);
+    int64_t att = 0, real = 0, rej = 0, cap = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : att, real, rej, cap)
+    for (int64_t i = 0; i < N; ++i) step_particle(S, i, n, Hn, Nmx, &att, &real, &rej, &cap);
     S->n_coll_attempts += att;
     S->n_real += real;
     S->n_rejected += rej;
@@ -858,6 +864,26 @@ static void step_once(orc_state *S)
     S->step = n + 1;
     S->n_out_of_grid = build_hist(S); /* f^{n+1} for the next step */
 }
+
+/* Test hook: advance only the listed particles by one time step (index S->step) against the
+ * current histogram; neither the step counter nor the histogram change. */
+void orc_step_particles(void *st, const int64_t *idx, int64_t n)
+{
+    orc_state *S = (orc_state *)st;
+    const orc_cfg *c = &S->cfg;
+    uint32_t Nmx[1296];
+    if (c->pauli_norm == ORC_PAULI_CURRENT_MAX) hist_max(S, Nmx);
+    else memcpy(Nmx, S->Nmax, sizeof(uint32_t) * S->Q);
+    int64_t att = 0, real = 0, rej = 0, cap = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : att, real, rej, cap)
+    for (int64_t j = 0; j < n; ++j) step_particle(S, idx[j], S->step, S->H, Nmx, &att, &real, &rej, &cap);
+}
+
+/* Test hook: set the step counter (the Philox counter word of the next step). */
+void orc_set_step(void *st, int64_t step) { ((orc_state *)st)->step = step; }
+
+/* Test hook: set the Pauli normaliser (e.g. that of another implementation's initial state). */
+void orc_set_nmax(void *st, const uint32_t *nmax) { memcpy(((orc_state *)st)->Nmax, nmax, sizeof(uint32_t) * ((orc_state *)st)->Q); }
 
 int orc_step(void *st, int64_t nsteps, int64_t moments_every)
 {
