@@ -324,7 +324,7 @@ __device__ __forceinline__ void flush_window(const uint32_t *swin, uint32_t *Hne
 }
 
 template <int P, int Q, typename R>
-__global__ void __launch_bounds__(kPhase1Threads)
+__global__ void __launch_bounds__(kPhase1Threads, (P * Q > 64) ? 2 : 3)
 k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
 {
     constexpr int PPT = Phase1PPT<P>::value;
@@ -549,7 +549,7 @@ __device__ __forceinline__ void stage(uint32_t *dst, const T &src)
 }
 
 template <int P, int Q, typename R>
-__global__ void __launch_bounds__(kPhase2Threads, 4)
+__global__ void __launch_bounds__(kPhase2Threads, (P * Q > 64) ? 3 : 4)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
     constexpr int G = GroupOf<Q>::G;
