@@ -42,10 +42,11 @@
  * them (e.g. as torch tensors), and passes the device pointers to pgc_init; they must stay valid
  * until pgc_destroy.  The context owns only host-side tables.  Device layouts:
  *   state   : R khat[2][P][ld], R = float (PGC_FP32) or double (PGC_FP64), c = x,y outermost,
- *             ld = N rounded up to a multiple of 32; 256-byte aligned base required;
- *   hist    : uint32 H[3][Q][Nk][Nk] (three rotating buffers; cell (r,l) of k is
- *             r = floor((kx+Lk)/dk), l = floor((ky+Lk)/dk));
- *   scratch : work space (collider queue, block partial sums, time series, counters).
+ *             ld = N rounded up to a multiple of 64; 256-byte aligned base required;
+ *   hist    : uint32 H[4][Q][Nk][Nk] (four rotating buffers, f^n in buffer n % 4; cell (r,l)
+ *             of k is r = floor((kx+Lk)/dk), l = floor((ky+Lk)/dk));
+ *   scratch : work space (two collider queues, collider bitmaps, block partial sums, time
+ *             series, counters, a device copy of the node tables).
  * All calls on a context are ordered on the CUDA stream given to pgc_init; calls that return
  * host data (pgc_moments, pgc_get_state, pgc_counters, pgc_reconstruct_f) synchronize it.
  *
@@ -145,8 +146,20 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
 
 /* Advance n_steps time steps (>= 0).  If moments_every > 0, the moments are recorded after
  * every step whose index is a multiple of moments_every (until max_outputs is reached, then
- * PGC_ENOMEM).  Asynchronous on the context's stream. */
+ * PGC_ENOMEM).  Asynchronous on the context's stream.
+ * A step is two kernels: the streaming kernel (drift, reconstruction, flight-time screen and
+ * histogram of every particle that provably does not collide) and the collider kernel (the
+ * collision loop of Algorithms 1/2 for the rest).  In the pipelined form (n_steps >= 2,
+ * pgc_set_pipeline) one launch per step n runs the streaming work of step n beside the collider
+ * work of step n - 1, whose particles are carried on through the drift and screen of step n
+ * (the streaming work skips them).  Trajectories, histograms and counters are the same in both
+ * forms; moment sums may differ in the last bits (FP32 summation order). */
 pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every);
+
+/* Switch the pipelined form of pgc_step on (1) or off (0).  Available and on by default when
+ * P * Q <= 64; PGC_EUNSUPPORTED for larger shapes (for P = 21, Q = 36 the streaming work alone
+ * fills the GPU). */
+pgc_status pgc_set_pipeline(pgc_ctx *ctx, int32_t on);
 
 /* Copy the recorded time series to the host (synchronizes).  Any pointer may be NULL.
  * h_t_fs[T]; h_mean[T][4], h_var[T][4] with columns (V_x m/s, V_y m/s, energy eV, J_x A/m);
@@ -175,9 +188,19 @@ pgc_status pgc_get_hist(pgc_ctx *ctx, uint32_t *h_hist, uint32_t *h_nmax);
  * stream around the two kernels of every `every`-th step; every = 0 switches it off and
  * clears the samples.  pgc_profile_read (synchronizes) returns the mean duration in ms of the
  * streaming kernel (phase 1: drift, reconstruction, flight-time screen, histogram) and of the
- * collider kernel (phase 2: collision loop of Algorithms 1/2) over the samples. */
+ * collider kernel (phase 2: collision loop of Algorithms 1/2) over the samples.  In the
+ * pipelined form the sampled steps are fused launches: ms_phase1 is the fused launch (the
+ * whole step) and ms_phase2 is 0. */
 pgc_status pgc_profile(pgc_ctx *ctx, int32_t every);
 pgc_status pgc_profile_read(pgc_ctx *ctx, double *ms_phase1, double *ms_phase2, int64_t *samples);
+
+/* Timeline of the sampled steps (synchronizes): h_t[k][4] = start and end of the streaming
+ * kernel, start and end of the collider kernel of the k-th sampled step, in ms after an event
+ * recorded before the first sampled step since pgc_profile (at most 4096 samples are kept).
+ * In the pipelined form a sampled step is its fused launch: the streaming interval is that
+ * launch and the collider interval is empty.  Copies min(max_samples, kept) samples;
+ * *n_samples = samples kept. */
+pgc_status pgc_profile_timeline(pgc_ctx *ctx, double *h_t, int64_t max_samples, int64_t *n_samples);
 
 /* Release the context (does not free the caller's buffers). NULL is a no-op. */
 void pgc_destroy(pgc_ctx *ctx);

@@ -55,12 +55,12 @@ pgc_status adj_layout(const pgc_ctx *ctx, int64_t n_steps, int32_t K, AdjLayout 
     L->ckpt_state = take((size_t)L->nseg * L->state);
     L->ckpt_hist = take((size_t)L->nseg * L->hist1);
     L->replay_state = take(L->state);
-    L->replay_hist = take((size_t)3 * ctx->b.hist_stride * 4);
+    L->replay_hist = take((size_t)kHistBufs * ctx->b.hist_stride * 4);
     L->stack_state = take((size_t)(K + 1) * L->state);
     L->stack_hist = take((size_t)K * L->hist1);
     L->lam = take(L->state);
     L->queue = take((size_t)ctx->b.N * 4);
-    L->qcount = take(4 * 4);
+    L->qcount = take(8 * 4);
     L->counters = take(8 * 8);
     L->part1 = take((size_t)kMaxGrid1 * Q * 3 * 8);
     L->part2 = take((size_t)kGrid2 * Q * 3 * 8);
@@ -124,7 +124,7 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
         const int64_t n0 = sgi * K, n1 = std::min<int64_t>(n_steps, n0 + K);
         e = cudaMemcpyAsync(w + L.ckpt_state + sgi * L.state, ctx->b.state, stbytes, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(w + L.ckpt_hist + sgi * L.hist1, ctx->b.hist + (int64_t)(ctx->step % 3) * ctx->b.hist_stride,
+            e = cudaMemcpyAsync(w + L.ckpt_hist + sgi * L.hist1, ctx->b.hist + (int64_t)(ctx->step % kHistBufs) * ctx->b.hist_stride,
                                 hbytes, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return afail(ctx, PGC_ECUDA, std::string("checkpoint: ") + cudaGetErrorString(e));
         st = pgc_step(ctx, n1 - n0, moments_every);
@@ -166,10 +166,14 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
     rb.state = w + L.replay_state;
     rb.hist = (uint32_t *)(w + L.replay_hist);
     rb.queue = (uint32_t *)(w + L.queue);
+    rb.queue_stride = 0;   // one queue: the replay runs the two-launch form of the step
     rb.qcount = (uint32_t *)(w + L.qcount);
     rb.counters = (unsigned long long *)(w + L.counters);
     rb.part1 = (double *)(w + L.part1);
+    rb.part1_stride = 0;
     rb.part2 = (double *)(w + L.part2);
+    rb.partN = nullptr;
+    rb.marks = nullptr;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -186,15 +190,15 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
     for (int64_t sgi = L.nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
         const int64_t n0 = sgi * K, n1 = std::min<int64_t>(n_steps, n0 + K);
         e = cudaMemcpyAsync(rb.state, w + L.ckpt_state + sgi * L.state, stbytes, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(rb.hist, 0, (size_t)3 * rb.hist_stride * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(rb.hist, 0, (size_t)kHistBufs * rb.hist_stride * 4, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(rb.hist + (int64_t)(n0 % 3) * rb.hist_stride, w + L.ckpt_hist + sgi * L.hist1, hbytes,
+            e = cudaMemcpyAsync(rb.hist + (int64_t)(n0 % kHistBufs) * rb.hist_stride, w + L.ckpt_hist + sgi * L.hist1, hbytes,
                                 cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(rb.qcount, 0, 4 * 4, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(rb.qcount, 0, 8 * 4, s);
         for (int64_t n = n0; n < n1 && e == cudaSuccess; ++n) {
             e = cudaMemcpyAsync(w + L.stack_state + (n - n0) * L.state, rb.state, stbytes, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(w + L.stack_hist + (n - n0) * L.hist1, rb.hist + (int64_t)(n % 3) * rb.hist_stride, hbytes,
+                e = cudaMemcpyAsync(w + L.stack_hist + (n - n0) * L.hist1, rb.hist + (int64_t)(n % kHistBufs) * rb.hist_stride, hbytes,
                                     cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = replay->step(n, false, s);
         }

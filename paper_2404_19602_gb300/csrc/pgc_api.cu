@@ -236,7 +236,7 @@ static void build_tables(const pgc_config &c, HostTables &t)
 struct FinArgs {
     double nq[64], w[64];
     double N, vF_ms, t_fs;
-    int Q, g1, g2;
+    int Q, g1, g2, g3;
 };
 
 // fixed-order reduction of the block partials, node values, mean and variance (Sec. 4.2);
@@ -244,7 +244,7 @@ struct FinArgs {
 // the blocks congruent to t / n3 (coalesced reads), then one thread per column adds the slots.
 constexpr int kFinThreads = 1024;
 __global__ void __launch_bounds__(kFinThreads)
-k_finalize(const double *part1, const double *part2, const __grid_constant__ FinArgs f, double *rec)
+k_finalize(const double *part1, const double *part2, const double *part3, const __grid_constant__ FinArgs f, double *rec)
 {
     __shared__ double red[kFinThreads];
     __shared__ double S[64 * 3];
@@ -255,6 +255,7 @@ k_finalize(const double *part1, const double *part2, const __grid_constant__ Fin
     if (slot < nslot) {
         for (int b = slot; b < f.g1; b += nslot) s += part1[(int64_t)b * n3 + col];
         for (int b = slot; b < f.g2; b += nslot) s += part2[(int64_t)b * n3 + col];
+        for (int b = slot; b < f.g3; b += nslot) s += part3[(int64_t)b * n3 + col];
     }
     red[t] = s;
     __syncthreads();
@@ -317,7 +318,8 @@ cudaError_t launch_finalize(const pgc_ctx *ctx, const double *part, int g1, doub
     f.Q = ctx->t.Q;
     f.g1 = g1;
     f.g2 = 0;
-    k_finalize<<<1, kFinThreads, 0, s>>>(part, nullptr, f, rec);
+    f.g3 = 0;
+    k_finalize<<<1, kFinThreads, 0, s>>>(part, nullptr, nullptr, f, rec);
     count_launch();
     return cudaGetLastError();
 }
@@ -337,15 +339,24 @@ static void *staging(pgc_ctx *ctx, size_t bytes)
     return ctx->pinned;
 }
 
+static constexpr size_t kMaxTimeline = 4096;  // samples kept for pgc_profile_timeline
+
 static void prof_collect(pgc_ctx *ctx)
 {
     for (int k = 0; k < ctx->prof_used; ++k) {
         float a = 0.f, b = 0.f;
-        if (cudaEventElapsedTime(&a, ctx->prof_ev[3 * k], ctx->prof_ev[3 * k + 1]) == cudaSuccess &&
-            cudaEventElapsedTime(&b, ctx->prof_ev[3 * k + 1], ctx->prof_ev[3 * k + 2]) == cudaSuccess) {
+        if (cudaEventElapsedTime(&a, ctx->prof_ev[4 * k], ctx->prof_ev[4 * k + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ctx->prof_ev[4 * k + 2], ctx->prof_ev[4 * k + 3]) == cudaSuccess) {
             ctx->prof_ms[0] += a;
             ctx->prof_ms[1] += b;
             ctx->prof_samples++;
+            if (ctx->prof_ref_set && ctx->prof_tl.size() < 4 * kMaxTimeline) {
+                float t[4];
+                bool ok = true;
+                for (int j = 0; j < 4 && ok; ++j) ok = cudaEventElapsedTime(&t[j], ctx->prof_ref, ctx->prof_ev[4 * k + j]) == cudaSuccess;
+                if (ok)
+                    for (int j = 0; j < 4; ++j) ctx->prof_tl.push_back(t[j]);
+            }
         }
     }
     ctx->prof_used = 0;
@@ -376,10 +387,10 @@ static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 namespace {
 struct Layout {
     int P = 1, Q = 1, d = 0;
-    int64_t ld = 0, hist_stride = 0;
+    int64_t ld = 0, hist_stride = 0, queue_stride = 0, mark_words = 0;
     size_t state = 0, hist = 0, scratch = 0;
     size_t off_queue = 0, off_qcount = 0, off_counters = 0, off_nmax = 0, off_part1 = 0, off_part2 = 0,
-           off_series = 0, off_recon = 0, off_tmpmax = 0;
+           off_partN = 0, off_marks = 0, off_tables = 0, off_series = 0, off_recon = 0, off_tmpmax = 0;
     int rec_len = 0;
 };
 }  // namespace
@@ -418,16 +429,21 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     L->ld = round_up(N, 64);
     L->state = (size_t)2 * L->P * L->ld * R;
     L->hist_stride = round_up((int64_t)L->Q * c->Nk * c->Nk, 64);
-    L->hist = (size_t)3 * L->hist_stride * 4;
+    L->hist = (size_t)kHistBufs * L->hist_stride * 4;
     L->rec_len = 1 + 4 * L->Q + 8;
+    L->queue_stride = round_up(N, 64);
+    L->mark_words = round_up((N + 31) / 32, 64);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
-    L->off_queue = take((size_t)N * 4);
-    L->off_qcount = take(4 * 4);
+    L->off_queue = take((size_t)2 * L->queue_stride * 4);
+    L->off_qcount = take(8 * 4);
     L->off_counters = take(8 * 8);
     L->off_nmax = take((size_t)L->Q * 4);
-    L->off_part1 = take((size_t)kMaxGrid1 * L->Q * 3 * 8);
+    L->off_part1 = take((size_t)2 * kMaxGrid1 * L->Q * 3 * 8);
     L->off_part2 = take((size_t)kGrid2 * L->Q * 3 * 8);
+    L->off_partN = take((size_t)2 * kGrid2 * L->Q * 3 * 8);
+    L->off_marks = take((size_t)kMarkSlots * L->mark_words * 4);
+    L->off_tables = take(kTableBytes);
     L->off_series = take((size_t)c->max_outputs * L->rec_len * 8);
     L->off_recon = take((size_t)c->Nk * c->Nk * 4);
     L->off_tmpmax = take(4);
@@ -482,8 +498,8 @@ static pgc_status observe_current(pgc_ctx *ctx, bool record, bool set_nmax)
 {
     cudaStream_t s = ctx->stream;
     cudaError_t e;
-    const int cur = (int)(ctx->step % 3);
-    if ((e = cudaMemsetAsync(ctx->b.hist, 0, (size_t)3 * ctx->b.hist_stride * 4, s)) != cudaSuccess)
+    const int cur = (int)(ctx->step % kHistBufs);
+    if ((e = cudaMemsetAsync(ctx->b.hist, 0, (size_t)kHistBufs * ctx->b.hist_stride * 4, s)) != cudaSuccess)
         return cuda_fail(ctx, e, "memset hist");
     if ((e = ctx->run->observe(cur, s)) != cudaSuccess) return cuda_fail(ctx, e, "observe");
     const int64_t cells = (int64_t)ctx->t.Nk * ctx->t.Nk;
@@ -501,7 +517,8 @@ static pgc_status observe_current(pgc_ctx *ctx, bool record, bool set_nmax)
         f.Q = ctx->t.Q;
         f.g1 = ctx->run->grid1();
         f.g2 = 0;
-        k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
+        f.g3 = 0;
+        k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1, nullptr, nullptr, f, ctx->series + ctx->T_out * ctx->rec_len);
         count_launch();
         ctx->T_out++;
     }
@@ -540,11 +557,17 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     b.hist = (uint32_t *)d_hist;
     b.hist_stride = L.hist_stride;
     b.queue = (uint32_t *)(scr + L.off_queue);
+    b.queue_stride = L.queue_stride;
     b.qcount = (uint32_t *)(scr + L.off_qcount);
     b.counters = (unsigned long long *)(scr + L.off_counters);
     b.nmax = (uint32_t *)(scr + L.off_nmax);
     b.part1 = (double *)(scr + L.off_part1);
+    b.part1_stride = (int64_t)kMaxGrid1 * L.Q * 3;
     b.part2 = (double *)(scr + L.off_part2);
+    b.partN = (double *)(scr + L.off_partN);
+    b.marks = (uint32_t *)(scr + L.off_marks);
+    b.mark_words = L.mark_words;
+    b.tables = scr + L.off_tables;
     b.recon_hist = (uint32_t *)(scr + L.off_recon);
     b.key0 = (uint32_t)cfg->seed;
     b.key1 = (uint32_t)(cfg->seed >> 32);
@@ -553,11 +576,15 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     ctx->tmp_max = (uint32_t *)(scr + L.off_tmpmax);
     ctx->rec_len = L.rec_len;
     ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
+    // the fused step overlaps the collider work with the streaming work; for the 36-node shape
+    // the streaming work alone fills the GPU
+    ctx->pipeline = ctx->run->fused() ? 1 : 0;
     if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
 
     cudaStream_t s = ctx->stream;
     if ((e = cudaMemsetAsync(d_scratch, 0, L.scratch, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(d_state, 0, L.state, s)) != cudaSuccess) {
+        (e = cudaMemsetAsync(d_state, 0, L.state, s)) != cudaSuccess ||
+        (e = ctx->run->upload_tables(s)) != cudaSuccess) {
         delete ctx->run; delete ctx;
         return fail(nullptr, PGC_ECUDA, std::string("memset: ") + cudaGetErrorString(e));
     }
@@ -588,6 +615,7 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
     if (ctx->T_out + outs > ctx->cfg.max_outputs) return fail(ctx, PGC_ENOMEM, "moment series would exceed max_outputs");
     cudaStream_t s = ctx->stream;
     const int64_t cells = (int64_t)ctx->t.Nk * ctx->t.Nk;
+    const int Q3 = ctx->t.Q * 3;
     FinArgs f{};
     for (int q = 0; q < ctx->t.Q; ++q) { f.nq[q] = ctx->t.nq[q]; f.w[q] = ctx->t.w[q]; }
     f.N = (double)ctx->b.N;
@@ -595,34 +623,93 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
     f.Q = ctx->t.Q;
     f.g1 = ctx->run->grid1();
     f.g2 = ctx->run->grid2();
-    for (int64_t k = 0; k < n_steps; ++k) {
-        const int64_t n = ctx->step;
-        const bool out = moments_every > 0 && ((n + 1) % moments_every == 0);
-        if (ctx->t.pauli_mode == PGC_PAULI_CURRENT_MAX) {
-            k_hist_max<<<ctx->t.Q, 256, 0, s>>>(ctx->b.hist + (int64_t)(n % 3) * ctx->b.hist_stride, cells, ctx->b.nmax);
-            count_launch();
+    auto is_out = [&](int64_t n) { return moments_every > 0 && ((n + 1) % moments_every == 0); };
+    auto hist_max = [&](int64_t n) {
+        if (ctx->t.pauli_mode != PGC_PAULI_CURRENT_MAX) return;
+        k_hist_max<<<ctx->t.Q, 256, 0, s>>>(ctx->b.hist + (int64_t)(n % kHistBufs) * ctx->b.hist_stride, cells, ctx->b.nmax);
+        count_launch();
+    };
+    // record of step n: phase-1 partials of step n (g1 blocks), phase-2 partials of step n (g2
+    // blocks) and, when phase 2 of step n - 1 carried particles into step n, its partials of step
+    // n (g3 blocks)
+    auto finalize = [&](int64_t n, int g2, int g3) {
+        f.t_fs = (n + 1) * ctx->t.dt;
+        f.g2 = g2;
+        f.g3 = g3;
+        const double *p3 = g3 > 0 ? ctx->b.partN + (n & 1) * (int64_t)kGrid2 * Q3 : nullptr;
+        k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1 + (n & 1) * ctx->b.part1_stride, ctx->b.part2, p3, f,
+                                             ctx->series + ctx->T_out * ctx->rec_len);
+        count_launch();
+        ctx->T_out++;
+    };
+    // kernel timing events of step n (4 per sample), or nullptr
+    auto prof_slot = [&](int64_t n, cudaEvent_t **out) -> cudaError_t {
+        *out = nullptr;
+        if (!(ctx->prof_every > 0 && (n % ctx->prof_every) == 0)) return cudaSuccess;
+        if (ctx->prof_used * 4 + 4 > (int)ctx->prof_ev.size()) {
+            cudaError_t se = cudaStreamSynchronize(s);
+            if (se != cudaSuccess) return se;
+            prof_collect(ctx);
         }
-        cudaEvent_t *ev = nullptr;
-        if (ctx->prof_every > 0 && (n % ctx->prof_every) == 0) {
-            if (ctx->prof_used * 3 + 3 > (int)ctx->prof_ev.size()) {
-                cudaError_t se = cudaStreamSynchronize(s);
-                if (se != cudaSuccess) return cuda_fail(ctx, se, "profile sync");
-                prof_collect(ctx);
-            }
-            ev = &ctx->prof_ev[(size_t)3 * ctx->prof_used++];
+        if (!ctx->prof_ref_set) {
+            cudaError_t re = cudaEventRecord(ctx->prof_ref, s);
+            if (re != cudaSuccess) return re;
+            ctx->prof_ref_set = true;
         }
-        cudaError_t e = ctx->run->step(n, out, s, ev);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
-        ctx->step = n + 1;
-        if (out) {
-            f.t_fs = ctx->step * ctx->t.dt;
-            k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1, ctx->b.part2, f, ctx->series + ctx->T_out * ctx->rec_len);
-            count_launch();
-            ctx->T_out++;
+        *out = &ctx->prof_ev[(size_t)4 * ctx->prof_used++];
+        return cudaSuccess;
+    };
+    const int64_t n0 = ctx->step;
+    const int g2 = ctx->run->grid2(), g2f = ctx->run->grid2f();
+    cudaError_t e = cudaSuccess;
+    if (!ctx->pipeline || n_steps < 2) {
+        for (int64_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
+            const int64_t n = n0 + k;
+            hist_max(n);
+            cudaEvent_t *ev = nullptr;
+            if ((e = prof_slot(n, &ev)) != cudaSuccess) break;
+            e = ctx->run->step(n, is_out(n), s, ev);
+            if (e == cudaSuccess && is_out(n)) finalize(n, g2, 0);
+        }
+    } else {
+        // Pipelined form: phase 1 of step n0, then one fused launch per step n (phase 1 of n
+        // beside phase 2 of n - 1, which carries its particles into step n), then phase 2 of the
+        // last step, so that the call ends on a step boundary.  The record of step n - 1 is
+        // complete after the fused launch of step n.
+        const int64_t n1 = n0 + n_steps - 1;
+        // the bitmap of step n0 may hold bits left by steps taken outside this context's kernels
+        e = cudaMemsetAsync(ctx->b.marks + (n0 % kMarkSlots) * ctx->b.mark_words, 0, (size_t)ctx->b.mark_words * 4, s);
+        if (e == cudaSuccess) {
+            hist_max(n0);
+            e = ctx->run->phase1(n0, is_out(n0), s);
+        }
+        for (int64_t n = n0 + 1; n <= n1 && e == cudaSuccess; ++n) {
+            hist_max(n - 1);
+            cudaEvent_t *ev = nullptr;
+            if ((e = prof_slot(n, &ev)) != cudaSuccess) break;
+            if (ev) cudaEventRecord(ev[0], s);
+            e = ctx->run->step_fused(n, is_out(n), is_out(n - 1), s);
+            if (ev) for (int j = 1; j < 4; ++j) cudaEventRecord(ev[j], s);
+            if (e == cudaSuccess && is_out(n - 1)) finalize(n - 1, g2f, n - 1 > n0 ? g2f : 0);
+        }
+        if (e == cudaSuccess) {
+            hist_max(n1);
+            e = ctx->run->phase2(n1, is_out(n1), s);
+            if (e == cudaSuccess && is_out(n1)) finalize(n1, g2, n1 > n0 ? g2f : 0);
         }
     }
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
+    ctx->step = n0 + n_steps;
+    return PGC_OK;
+}
+
+pgc_status pgc_set_pipeline(pgc_ctx *ctx, int32_t on)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(ctx, PGC_EINVAL, "on must be 0 or 1");
+    if (on && !ctx->run->fused()) return fail(ctx, PGC_EUNSUPPORTED, "no pipelined step kernel for this shape (P * Q > 64)");
+    ctx->pipeline = on;
     return PGC_OK;
 }
 
@@ -719,7 +806,7 @@ pgc_status pgc_get_hist(pgc_ctx *ctx, uint32_t *h_hist, uint32_t *h_nmax)
 {
     if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
     if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
-    const int cur = (int)(ctx->step % 3);
+    const int cur = (int)(ctx->step % kHistBufs);
     cudaError_t e = cudaSuccess;
     if (h_hist)
         e = cudaMemcpyAsync(h_hist, ctx->b.hist + (int64_t)cur * ctx->b.hist_stride,
@@ -766,16 +853,32 @@ pgc_status pgc_profile(pgc_ctx *ctx, int32_t every)
     if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
     if (every < 0) return fail(ctx, PGC_EINVAL, "every < 0");
     if (every > 0 && ctx->prof_ev.empty()) {
-        ctx->prof_ev.resize(3 * 256);
+        ctx->prof_ev.resize(4 * 256);
         for (auto &ev : ctx->prof_ev) {
             cudaError_t e = cudaEventCreate(&ev);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "event create");
         }
+        cudaError_t e = cudaEventCreate(&ctx->prof_ref);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event create");
     }
     ctx->prof_every = every;
     ctx->prof_used = 0;
     ctx->prof_ms[0] = ctx->prof_ms[1] = 0.0;
     ctx->prof_samples = 0;
+    ctx->prof_ref_set = false;
+    ctx->prof_tl.clear();
+    return PGC_OK;
+}
+
+pgc_status pgc_profile_timeline(pgc_ctx *ctx, double *h_t, int64_t max_samples, int64_t *n_samples)
+{
+    if (!ctx || !n_samples || max_samples < 0 || (max_samples > 0 && !h_t)) return fail(ctx, PGC_EINVAL, "bad arguments");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "profile sync");
+    prof_collect(ctx);
+    const int64_t n = std::min<int64_t>(max_samples, (int64_t)(ctx->prof_tl.size() / 4));
+    for (int64_t k = 0; k < 4 * n; ++k) h_t[k] = ctx->prof_tl[(size_t)k];
+    *n_samples = (int64_t)(ctx->prof_tl.size() / 4);
     return PGC_OK;
 }
 
@@ -796,6 +899,7 @@ void pgc_destroy(pgc_ctx *ctx)
 {
     if (!ctx) return;
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
+    if (ctx->prof_ref) cudaEventDestroy(ctx->prof_ref);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx->run;
     delete ctx;

@@ -26,7 +26,7 @@ struct CaseDev {
     Nodes<P, Q, R> nd;         // the case's tables (basis tables are identical across cases)
     R *khat;
     int64_t N, ld;
-    uint32_t *hist;            // three rotating buffers of the case
+    uint32_t *hist;            // kHistBufs rotating buffers of the case
     int64_t hist_stride;
     const uint32_t *nmax;
     unsigned long long *counters;
@@ -81,7 +81,7 @@ k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
     extern __shared__ uint32_t swin[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t step = *a.d_step;
-    const int nxt = (int)((step + 1) % 3), clr = (int)((step + 2) % 3);
+    const int nxt = (int)((step + 1) % kHistBufs), clr = (int)((step + 2) % kHistBufs);
     const bool out = a.moments_every > 0 && ((step + 1) % a.moments_every == 0);
     if (blockIdx.x == 0 && threadIdx.x == 0) a.qcount[(step + 1) & 1] = 0u;
     for (int j = threadIdx.x; j <= a.ncases; j += blockDim.x) stile[j] = a.tile0s[j];
@@ -145,16 +145,14 @@ __global__ void __launch_bounds__(kPhase2Threads)
 k_phase2_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
 {
     constexpr int G = GroupOf<Q>::G;
-    __shared__ __align__(16) uint32_t sph[(sizeof(Phys<R>) + 3) / 4];
     __shared__ int64_t sbase[kBatchMaxCases + 1];
     __shared__ uint32_t scnt[kBatchMaxCases][5];   // per-case counters of this block
-    stage(sph, a.ph);
     for (int j = threadIdx.x; j <= a.ncases; j += blockDim.x) sbase[j] = a.bases[j];
     for (int j = threadIdx.x; j < a.ncases * 5; j += blockDim.x) (&scnt[0][0])[j] = 0u;
     __syncthreads();
-    const Phys<R> &ph = *reinterpret_cast<const Phys<R> *>(sph);
+    const Phys<R> &ph = a.ph;   // read alike by all lanes: stays in the parameter bank
     const int64_t step = *a.d_step;
-    const int cur = (int)(step % 3), nxt = (int)((step + 1) % 3);
+    const int cur = (int)(step % kHistBufs), nxt = (int)((step + 1) % kHistBufs);
     const bool out = a.moments_every > 0 && ((step + 1) % a.moments_every == 0);
     const uint32_t count = a.qcount[step & 1];
 

@@ -233,7 +233,7 @@ pgc_status pgc_batch_step(pgc_batch *b, int64_t n_steps, int32_t moments_every, 
     for (; done < n_steps && e == cudaSuccess; ++done) e = b->run->step(s);
     // the single-case collider counters must start at zero if a context is stepped alone later
     for (pgc_ctx *c : b->ctxs)
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->b.qcount, 0, 4 * sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->b.qcount, 0, 8 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return batch_fail(b, PGC_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
     for (pgc_ctx *c : b->ctxs) {
         c->step += n_steps;

@@ -23,12 +23,16 @@ struct pgc_ctx {
     bool failed = false;
     bool sampled = false;  // state comes from the initial Fermi-Dirac sampling (no upload since)
     std::string err;
+    int pipeline = 1;  // pipelined (fused) form of multi-step pgc_step calls (pgc_set_pipeline)
     // kernel timing samples (pgc_profile): events around phase 1 / phase 2 of sampled steps
     int prof_every = 0;
-    std::vector<cudaEvent_t> prof_ev;  // 3 per sample
+    std::vector<cudaEvent_t> prof_ev;  // 4 per sample
     int prof_used = 0;
     double prof_ms[2] = {0.0, 0.0};
     int64_t prof_samples = 0;
+    cudaEvent_t prof_ref = nullptr;    // recorded before the first sampled step
+    bool prof_ref_set = false;
+    std::vector<double> prof_tl;       // [sample][4] ms after prof_ref: phase-1 start/end, phase-2 start/end
     // pinned host staging buffer of the state transfers (allocated on first use)
     void *pinned = nullptr;
     size_t pinned_bytes = 0;

@@ -2,7 +2,7 @@
 // (arXiv:2404.19602, Algorithm 1 for P = Q = 1, Algorithm 2 otherwise), templated on the gPC
 // basis size P, the number of quadrature nodes Q and the arithmetic type R.
 //
-// One time step n is two launches on the context stream:
+// One time step n is two launches:
 //   k_phase1 (every particle, streaming): drift of the coefficients (Eq. (17), Sec. 4.1),
 //       reconstruction at the Q nodes (Eq. (23)), first flight-time draw, and a conservative
 //       rate bound that proves "no collision in this step" for most particles; those are
@@ -13,6 +13,13 @@
 //       Pauli test against f^n, then the histogram f^{n+1} and moments of the final state.
 // On moment steps a one-block k_finalize reduces the block partial sums in a fixed order and
 // writes the node values, mean and variance of the record (Sec. 4.2).
+//
+// Pipelined form (several steps per call): k_phase2<EXT = true> of step n, after the collision
+// loop of a queued particle, carries that particle on through the drift and the flight-time
+// screen of step n + 1 (finishing it there, or queueing it for step n + 1), and k_phase1 of step
+// n + 1 skips the particles queued at step n (a bitmap).  The two kernels then touch disjoint
+// particles and buffers and run concurrently on two streams; every particle undergoes the same
+// arithmetic as in the two-launch form, so the trajectories are identical.
 #pragma once
 
 #include "pgc_device.cuh"
@@ -28,6 +35,13 @@ constexpr int kGrid2 = 608;       // phase-2 blocks (grid-stride over the queue)
 // per block.  Cells outside the window go straight to the global histogram.
 constexpr int kWin = 32;
 constexpr int kWinWords = kWin * kWin / 2;
+// Rotating buffers.  Histogram f^n lives in buffer n % kHistBufs: while phase 2 of step n - 1
+// (reading f^{n-1}, writing f^n and f^{n+1}) runs beside phase 1 of step n (writing f^{n+1},
+// clearing f^{n+2}), four buffers are in use.  Collider counters: n % 3; queues and moment
+// partials: n % 2; collider bitmaps: n % 3.
+constexpr int kHistBufs = 4;
+constexpr int kQSlots = 3;
+constexpr int kMarkSlots = 3;
 
 // Quadrature / basis tables of one context (Sec. 4.1).
 template <int P, int Q, typename R>
@@ -63,6 +77,8 @@ struct StepArgs {
     uint32_t *queue;         // [N]
     uint32_t *qcount;        // collider count of this step
     uint32_t *qcount_next;   // counter of the next step (zeroed by phase 1)
+    uint32_t *tilectr;       // phase-1 tile counter of this step (nullptr: static tile assignment)
+    uint32_t *tilectr_next;  // tile counter of the next step (zeroed by phase 1)
     double *part1;           // [gridDim(phase1)][Q*3]
     double *part2;           // [kGrid2][Q*3]
     unsigned long long *counters;
@@ -70,6 +86,18 @@ struct StepArgs {
     int32_t out_step;        // 1: accumulate the moments of the post-step state
     int32_t win_r0;          // first row / column of the shared-memory window
     int32_t use_win;         // 1: phase 1 counts into the shared-memory window
+    // collider bitmaps (bit i of word i / 32), all optional (nullptr)
+    const uint32_t *skip;    // phase 1: particles queued at step n - 1, owned by a concurrent phase 2
+    uint32_t *mark;          // phase 1: set for every particle queued at step n
+    uint32_t *mark_clear;    // phase 1: bitmap of step n + 1, cleared
+    int64_t mark_words;      // words per bitmap (multiple of 4)
+    // phase 2 continuation into step n + 1 (k_phase2<EXT = true>)
+    uint32_t *Hnext2;        // f^{n+2}
+    uint32_t *queue_next;    // collider queue of step n + 1 (its counter is qcount_next)
+    uint32_t *mark_next;     // bitmap of step n + 1
+    double *partN;           // [kGrid2][Q*3] moments of step n + 1 of the particles finished here
+    int32_t out_next;        // 1: step n + 1 is a moment step
+    const Nodes<P, Q, R> *nd_dev;  // device copy of nd (phase 2 stages it into shared memory)
 };
 
 template <typename T>
@@ -78,6 +106,24 @@ __device__ __forceinline__ T warp_sum(T v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// |k|^2 and the screen of the first flight time with an explicit operation order, so that
+// phase 1 and the continuation in phase 2 take bit-identical decisions.
+template <typename R>
+__device__ __forceinline__ R knorm2(R kx, R ky)
+{
+    if constexpr (sizeof(R) == 8) return __fma_rn(kx, kx, __dmul_rn(ky, ky));
+    else return __fmaf_rn(kx, kx, __fmul_rn(ky, ky));
+}
+
+template <int P, int Q, typename R>
+__device__ __forceinline__ bool screen_maybe(const Phys<R> &ph, const Nodes<P, Q, R> &nd, R kkmax, uint32_t xi_bits)
+{
+    const R lnxi = -rlog<R>(u01<R>(xi_bits));
+    const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
+    const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
+    return lnxi < gub * ph.dt;
 }
 
 template <int P, int Q, typename R>
@@ -146,6 +192,31 @@ __device__ __forceinline__ void recon_all(const Nodes<P, Q, R> &nd, const R cx[P
     }
 }
 
+// The value recon_all produces at node q (same operations in the same order).
+template <int P, int Q, typename R>
+__device__ __forceinline__ void recon_at(const Nodes<P, Q, R> &nd, int q, const R cx[P], const R cy[P], R &kx, R &ky)
+{
+    if constexpr (TensorShape<P, Q>::value) {
+        const int q1 = q / 6, q2 = q - 6 * (q / 6);
+        R sx2 = (R)0, sy2 = (R)0;
+#pragma unroll
+        for (int h2 = 0; h2 < 6; ++h2) {
+            R sx = (R)0, sy = (R)0;
+#pragma unroll
+            for (int h1 = 0; h1 + h2 <= 5; ++h1) {
+                sx += cx[hidx2(h1, h2)] * nd.a1[q1 * 6 + h1];
+                sy += cy[hidx2(h1, h2)] * nd.a1[q1 * 6 + h1];
+            }
+            sx2 += sx * nd.b2[q2 * 6 + h2];
+            sy2 += sy * nd.b2[q2 * 6 + h2];
+        }
+        kx = sx2;
+        ky = sy2;
+    } else {
+        recon_node(nd, q, cx, cy, kx, ky);
+    }
+}
+
 // group velocity (units of vF) and energy at one node (Sec. 2).  The warp partial sums are
 // taken in R (FP32 in the production mode, FP64 in the FP64 mode) and accumulated in FP64.
 template <typename R>
@@ -162,6 +233,11 @@ __device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, R
 // coefficient plane with one 16-byte load (float4 / 2 x double2); the ensemble is streamed once.
 // ------------------------------------------------------------------------------------------
 template <int P> struct Phase1PPT { static constexpr int value = (P <= 8) ? 4 : 1; };
+// resident blocks per SM the streaming kernels are compiled for: three for the small FP32
+// shapes, two (more registers, no spills) for 36 nodes and for FP64
+template <int P, int Q, typename R> struct kPhase1MinBlocks {
+    static constexpr int value = (P * Q > 64 || sizeof(R) == 8) ? 2 : 3;
+};
 
 template <typename R, int PPT>
 __device__ __forceinline__ void load_vec(const R *p, R v[PPT])
@@ -203,6 +279,8 @@ struct P1Target {
     uint32_t *queue;          // collider queue
     uint32_t qoffset;         // added to the particle index in queue entries
     uint32_t key0, key1, stream_id, step;
+    const uint32_t *skip = nullptr;  // optional: particles left to a concurrent phase 2 (not touched here)
+    uint32_t *mark = nullptr;        // optional: bitmap of the particles queued here
 };
 
 // One pass of a block over blockDim * PPT consecutive particles starting at i0 + threadIdx*PPT:
@@ -218,6 +296,8 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
     R cx[PPT][P], cy[PPT][P];
     bool finished[PPT];
     const bool any = i0 < t.N;
+    // i0 is a multiple of PPT, so its PPT bits lie in one word
+    const uint32_t skipbits = (t.skip && any) ? (t.skip[i0 >> 5] >> (i0 & 31)) & ((1u << PPT) - 1u) : 0u;
     if (any) {
 #pragma unroll
         for (int h = 0; h < P; ++h) {
@@ -237,7 +317,14 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
                     if (i0 + e < t.N) cx[e][h] -= nd.dhat[h];
                     v[e] = cx[e][h];
                 }
-                store_vec<R, PPT>(t.khat + (int64_t)h * t.ld + i0, v);
+                if (skipbits == 0u) {
+                    store_vec<R, PPT>(t.khat + (int64_t)h * t.ld + i0, v);
+                } else {
+                    // a skipped particle is being written by phase 2: element-wise stores
+#pragma unroll
+                    for (int e = 0; e < PPT; ++e)
+                        if (!((skipbits >> e) & 1u) && i0 + e < t.N) t.khat[(int64_t)h * t.ld + i0 + e] = v[e];
+                }
             }
     }
 #pragma unroll
@@ -245,20 +332,17 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
         const int64_t i = i0 + e;
         finished[e] = false;
         bool maybe = false;
-        if (any && i < t.N) {
+        if (any && i < t.N && !((skipbits >> e) & 1u)) {
             // reconstruction, cells and the bound on the majorant
             int rl[Q];   // cell (row << 16) | column; -1 outside the grid
             R kkmax = (R)0;
             recon_all(nd, cx[e], cy[e], [&](int q, R kx, R ky) {
                 int r, l;
                 rl[q] = cell_rl(ph, kx, ky, r, l) ? ((r << 16) | l) : -1;
-                kkmax = fmax(kkmax, kx * kx + ky * ky);
+                kkmax = fmax(kkmax, knorm2(kx, ky));
             });
             const U4 r = philox4x32_10((uint32_t)i, t.stream_id, t.step, 0u, t.key0, t.key1);
-            const R lnxi = -rlog<R>(u01<R>(r.x));
-            const R emax = rsqrt_<R>(ph.hvF2 * kkmax + nd.eps0_max * nd.eps0_max);
-            const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
-            maybe = lnxi < gub * ph.dt;
+            maybe = screen_maybe(ph, nd, kkmax, r.x);
             if (!maybe) {
                 finished[e] = true;
 #pragma unroll
@@ -280,7 +364,10 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
             uint32_t basepos = 0;
             if (lane == leader) basepos = atomicAdd(t.qcount, (uint32_t)__popc(mask));
             basepos = __shfl_sync(0xffffffffu, basepos, leader);
-            if (maybe) t.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = t.qoffset + (uint32_t)i;
+            if (maybe) {
+                t.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = t.qoffset + (uint32_t)i;
+                if (t.mark) atomicOr(&t.mark[i >> 5], 1u << (i & 31));
+            }
         }
     }
     if (out_step) {
@@ -323,41 +410,64 @@ __device__ __forceinline__ void flush_window(const uint32_t *swin, uint32_t *Hne
     }
 }
 
+// Phase 1 of one block, block bid of the nb blocks doing phase 1.  Tiles of blockDim * PPT
+// particles: taken from the step's tile counter when there is one (blocks that start late take
+// fewer), else every nb-th tile.  swin: dynamic shared memory of the histogram window.
 template <int P, int Q, typename R>
-__global__ void __launch_bounds__(kPhase1Threads, (P * Q > 64) ? 2 : 3)
-k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
+__device__ __forceinline__ void phase1_block(const StepArgs<P, Q, R> &a, int bid, int nb, uint32_t *swin)
 {
     constexpr int PPT = Phase1PPT<P>::value;
     constexpr int NW = kPhase1Threads / 32;
     __shared__ double smom[NW][Q * 3];
-    extern __shared__ uint32_t swin[];   // [Q][kWinWords] when a.use_win
+    __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.use_win)
         for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) swin[j] = 0u;
+    if (a.out_step)
+        for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
     __syncthreads();
 
     // housekeeping for the next steps
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.qcount_next = 0u;
+    if (bid == 0 && threadIdx.x == 0) {
+        *a.qcount_next = 0u;
+        if (a.tilectr_next) *a.tilectr_next = 0u;
+    }
     {
         uint4 *hc = reinterpret_cast<uint4 *>(a.Hclear);
         const int64_t n4 = a.hist_elems >> 2;
-        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n4;
-             j += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < n4; j += (int64_t)nb * blockDim.x)
             hc[j] = make_uint4(0u, 0u, 0u, 0u);
-        if (blockIdx.x == 0)
+        if (bid == 0)
             for (int64_t j = (n4 << 2) + threadIdx.x; j < a.hist_elems; j += blockDim.x) a.Hclear[j] = 0u;
+        if (a.mark_clear) {
+            uint4 *mc = reinterpret_cast<uint4 *>(a.mark_clear);
+            for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < (a.mark_words >> 2); j += (int64_t)nb * blockDim.x)
+                mc[j] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
-    if (a.out_step)
-        for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
 
     P1Target<R> t;
     t.khat = a.khat; t.N = a.N; t.ld = a.ld; t.Hnext = a.Hnext; t.qcount = a.qcount; t.queue = a.queue;
     t.qoffset = 0u; t.key0 = a.key0; t.key1 = a.key1; t.stream_id = a.stream_id; t.step = a.step;
+    t.skip = a.skip; t.mark = a.mark;
     unsigned int oog = 0u;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * PPT;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT; base < a.N; base += stride)
-        phase1_pass<P, Q, R>(a.ph, a.nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
-                             a.out_step != 0, smom[warp], oog);
+    const int64_t tile = (int64_t)blockDim.x * PPT;
+    if (a.tilectr) {
+        const int64_t ntiles = (a.N + tile - 1) / tile;
+        for (;;) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(a.tilectr, 1u);
+            __syncthreads();
+            const int64_t tl = s_tile;
+            __syncthreads();   // every thread has read s_tile before it is overwritten
+            if (tl >= ntiles) break;
+            phase1_pass<P, Q, R>(a.ph, a.nd, t, tl * tile + (int64_t)threadIdx.x * PPT, swin, a.win_r0,
+                                 a.use_win != 0, a.out_step != 0, smom[warp], oog);
+        }
+    } else {
+        for (int64_t base = (int64_t)bid * tile; base < a.N; base += (int64_t)nb * tile)
+            phase1_pass<P, Q, R>(a.ph, a.nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
+                                 a.out_step != 0, smom[warp], oog);
+    }
     oog = warp_sum(oog);
     if (lane == 0 && oog) atomicAdd(&a.counters[4], (unsigned long long)oog);
     __syncthreads();
@@ -367,9 +477,17 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
             double s = 0.0;
 #pragma unroll
             for (int w = 0; w < NW; ++w) s += smom[w][j];
-            a.part1[(int64_t)blockIdx.x * (Q * 3) + j] = s;
+            a.part1[(int64_t)bid * (Q * 3) + j] = s;
         }
     }
+}
+
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(kPhase1Threads, kPhase1MinBlocks<P, Q, R>::value)
+k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
+{
+    extern __shared__ uint32_t swin[];   // [Q][kWinWords] when a.use_win
+    phase1_block<P, Q, R>(a, blockIdx.x, gridDim.x, swin);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -417,13 +535,21 @@ struct P2Target {
     double *mom;              // [Q*3] moment accumulators (shared or global), on moment steps
     uint32_t key0, key1, stream_id, step;
     bool out_step;
+    // continuation into step n + 1 (EXT)
+    uint32_t *Hnext2 = nullptr;      // f^{n+2}
+    uint32_t *queue_next = nullptr, *qcount_next = nullptr, *mark_next = nullptr;
+    double *momN = nullptr;          // [Q*3] moments of step n + 1
+    bool out_next = false;
 };
 
 struct P2Counts { unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0; };
 
 // The collision loop of Algorithm 1 / 2 for particle i, carried by the G lanes of a group (lane r
-// owns nodes r, r + G, ...), then the histogram f^{n+1} and moments of its final state.
-template <int P, int Q, typename R>
+// owns nodes r, r + G, ...), then the histogram f^{n+1} and moments of its final state.  With
+// EXT, the particle then goes through step n + 1 as far as phase 1 would take it: drift,
+// reconstruction, flight-time screen, and either the histogram f^{n+2} and moments of step n + 1
+// or a place in the collider queue of step n + 1.
+template <int P, int Q, typename R, bool EXT = false>
 __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const P2Target<R> &t,
                                                  int64_t i, int r, unsigned gmask, P2Counts &cnt)
 {
@@ -513,7 +639,13 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
         dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
     }
-    if (touched) {
+    if constexpr (EXT) {
+        // drift of step n + 1 (before the store: the stored state is the post-drift one, as phase 1 leaves it)
+#pragma unroll
+        for (int h = 0; h < P; ++h)
+            if (nd.drift_mask & (1u << h)) cx[h] -= nd.dhat[h];
+    }
+    if (touched || (EXT && nd.drift_mask != 0u)) {
         // lane h of the group writes coefficient h (x and y planes)
         for (int h = r; h < P; h += G) {
             R vx = cx[0], vy = cy[0];
@@ -538,6 +670,45 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             atomicAdd(&t.mom[q * 3 + 2], (double)e);
         }
     }
+    if constexpr (EXT) {
+        // step n + 1 up to the flight-time screen, with the operations of phase 1
+        int cl2[NPL];
+        R kk = (R)0;
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            cl2[s] = -1;
+            if (q < Q) {
+                R x, y;
+                recon_at(nd, q, cx, cy, x, y);
+                cl2[s] = cell_of(ph, x, y);
+                kk = fmax(kk, knorm2(x, y));
+            }
+        }
+        const R kkmax = group_max<G>(kk, gmask);
+        const U4 r1 = philox4x32_10((uint32_t)i, t.stream_id, t.step + 1u, 0u, t.key0, t.key1);
+        if (!screen_maybe(ph, nd, kkmax, r1.x)) {
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q >= Q) continue;
+                if (cl2[s] >= 0) atomicAdd(&t.Hnext2[(int64_t)q * NN + cl2[s]], 1u);
+                else ++cnt.oog;
+                if (t.out_next) {
+                    R x, y, vx, vy, e;
+                    recon_node(nd, q, cx, cy, x, y);
+                    observe(ph, x, y, nd.eps0[q], vx, vy, e);
+                    atomicAdd(&t.momN[q * 3 + 0], (double)vx);
+                    atomicAdd(&t.momN[q * 3 + 1], (double)vy);
+                    atomicAdd(&t.momN[q * 3 + 2], (double)e);
+                }
+            }
+        } else if (r == 0) {
+            const uint32_t pos = atomicAdd(t.qcount_next, 1u);
+            t.queue_next[pos] = (uint32_t)i;
+            atomicOr(&t.mark_next[i >> 5], 1u << (i & 31));
+        }
+    }
 }
 
 // Copy a trivially-copyable table into shared memory (all threads; caller synchronises).
@@ -548,37 +719,49 @@ __device__ __forceinline__ void stage(uint32_t *dst, const T &src)
     for (int j = threadIdx.x; j < (int)(sizeof(T) / 4); j += blockDim.x) dst[j] = s[j];
 }
 
-template <int P, int Q, typename R>
-__global__ void __launch_bounds__(kPhase2Threads, (P * Q > 64) ? 3 : 4)
-k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
+// Phase 2 of one block, block bid of the nb blocks doing phase 2 (any block size that is a
+// multiple of the group size).
+template <int P, int Q, typename R, bool EXT>
+__device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid, int nb)
 {
     constexpr int G = GroupOf<Q>::G;
     __shared__ double smom[Q * 3];
+    __shared__ double smomN[EXT ? Q * 3 : 1];
     __shared__ unsigned long long scnt[5];
-    // The lanes of a group read different nodes' tables: staged in shared memory (the constant
-    // bank serialises divergent addresses).
-    __shared__ __align__(16) uint32_t sph[(sizeof(Phys<R>) + 3) / 4];
+    // The lanes of a group read different nodes' entries of the node tables: staged in shared
+    // memory from their device copy (divergent reads of the parameter bank serialise).  The
+    // physics constants are read by all lanes alike and stay in the parameter bank.
     __shared__ __align__(16) uint32_t snd[(sizeof(Nodes<P, Q, R>) + 3) / 4];
     if (threadIdx.x < 5) scnt[threadIdx.x] = 0ull;
     for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) smom[j] = 0.0;
-    stage(sph, a.ph);
-    stage(snd, a.nd);
+    if constexpr (EXT)
+        for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) smomN[j] = 0.0;
+    if (a.nd_dev) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(a.nd_dev);
+        for (int j = threadIdx.x; j < (int)(sizeof(Nodes<P, Q, R>) / 4); j += blockDim.x) snd[j] = src[j];
+    } else {
+        stage(snd, a.nd);
+    }
     __syncthreads();
 
-    const Phys<R> &ph = *reinterpret_cast<const Phys<R> *>(sph);
+    const Phys<R> &ph = a.ph;
     const Nodes<P, Q, R> &nd = *reinterpret_cast<const Nodes<P, Q, R> *>(snd);
     const uint32_t count = *a.qcount;
     P2Counts cnt;
     P2Target<R> t;
     t.khat = a.khat; t.ld = a.ld; t.Hcur = a.Hcur; t.Hnext = a.Hnext; t.nmax = a.nmax; t.mom = smom;
     t.key0 = a.key0; t.key1 = a.key1; t.stream_id = a.stream_id; t.step = a.step; t.out_step = a.out_step != 0;
+    if constexpr (EXT) {
+        t.Hnext2 = a.Hnext2; t.queue_next = a.queue_next; t.qcount_next = a.qcount_next; t.mark_next = a.mark_next;
+        t.momN = smomN; t.out_next = a.out_next != 0;
+    }
 
     const int lane = threadIdx.x & 31;
     const int r = lane % G;                                  // lane in the group
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
-    const uint32_t gid = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const uint32_t ngroups = gridDim.x * blockDim.x / G;
-    for (uint32_t j = gid; j < count; j += ngroups) collide_particle<P, Q, R>(ph, nd, t, a.queue[j], r, gmask, cnt);
+    const uint32_t gid = ((uint32_t)bid * blockDim.x + threadIdx.x) / G;
+    const uint32_t ngroups = (uint32_t)nb * blockDim.x / G;
+    for (uint32_t j = gid; j < count; j += ngroups) collide_particle<P, Q, R, EXT>(ph, nd, t, a.queue[j], r, gmask, cnt);
 
     if (cnt.att) atomicAdd(&scnt[0], cnt.att);
     if (cnt.chg) atomicAdd(&scnt[1], cnt.chg);
@@ -587,9 +770,32 @@ k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
     if (cnt.oog) atomicAdd(&scnt[4], cnt.oog);
     __syncthreads();
     if (threadIdx.x < 5 && scnt[threadIdx.x]) atomicAdd(&a.counters[threadIdx.x], scnt[threadIdx.x]);
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&a.counters[5], (unsigned long long)count);
+    if (threadIdx.x == 0 && bid == 0) atomicAdd(&a.counters[5], (unsigned long long)count);
     if (a.out_step)
-        for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) a.part2[(int64_t)blockIdx.x * (Q * 3) + j] = smom[j];
+        for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) a.part2[(int64_t)bid * (Q * 3) + j] = smom[j];
+    if constexpr (EXT)
+        if (a.out_next)
+            for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) a.partN[(int64_t)bid * (Q * 3) + j] = smomN[j];
+}
+
+template <int P, int Q, typename R, bool EXT>
+__global__ void __launch_bounds__(kPhase2Threads, (P * Q > 64) ? 3 : 4)
+k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
+{
+    phase2_block<P, Q, R, EXT>(a, blockIdx.x, gridDim.x);
+}
+
+// One launch per time step in the pipelined form: blocks [0, nb2) run phase 2 of step n - 1 with
+// the continuation into step n (a2), the others phase 1 of step n (a1, tiles from the tile
+// counter, skipping the particles queued at step n - 1).  The two roles touch disjoint particles;
+// shared buffers are only added to (histograms, queue of step n, bitmap of step n).
+template <int P, int Q, typename R>
+__global__ void __launch_bounds__(kPhase1Threads, kPhase1MinBlocks<P, Q, R>::value)
+k_step(const __grid_constant__ StepArgs<P, Q, R> a1, const __grid_constant__ StepArgs<P, Q, R> a2, int nb2)
+{
+    extern __shared__ uint32_t swin[];
+    if ((int)blockIdx.x < nb2) phase2_block<P, Q, R, true>(a2, blockIdx.x, nb2);
+    else phase1_block<P, Q, R>(a1, blockIdx.x - nb2, gridDim.x - nb2, swin);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -36,14 +36,20 @@ struct HostTables {
 struct DevBuffers {
     void *state = nullptr;          // R [2][P][ld]
     int64_t N = 0, ld = 0;
-    uint32_t *hist = nullptr;       // [3][hist_stride]
+    uint32_t *hist = nullptr;       // [kHistBufs][hist_stride]
     int64_t hist_stride = 0;        // elements per buffer (>= Q*Nk*Nk, multiple of 64)
-    uint32_t *queue = nullptr;      // [N]
-    uint32_t *qcount = nullptr;     // [4]
+    uint32_t *queue = nullptr;      // [2][queue_stride] (queue_stride 0: one queue for both slots)
+    int64_t queue_stride = 0;
+    uint32_t *qcount = nullptr;     // [8]: collider counters n % 3 in [0, 3), phase-1 tile counters n % 3 in [4, 7)
     unsigned long long *counters = nullptr;  // [8]
     uint32_t *nmax = nullptr;       // [Q]
-    double *part1 = nullptr;        // [kMaxGrid1][Q*3]
+    double *part1 = nullptr;        // [2][kMaxGrid1][Q*3] (part1_stride 0: one slot)
+    int64_t part1_stride = 0;
     double *part2 = nullptr;        // [kGrid2][Q*3]
+    double *partN = nullptr;        // [2][kGrid2][Q*3] or nullptr (pipelined steps only)
+    uint32_t *marks = nullptr;      // [kMarkSlots][mark_words] collider bitmaps or nullptr (pipelined steps only)
+    int64_t mark_words = 0;
+    void *tables = nullptr;         // device copy of the node tables (kTableBytes) or nullptr
     uint32_t *recon_hist = nullptr; // [Nk*Nk]
     uint32_t key0 = 0, key1 = 0, stream_id = 0;
 };
@@ -53,6 +59,7 @@ public:
     virtual ~Runner() {}
     virtual int grid1() const = 0;
     virtual int grid2() const = 0;
+    virtual int grid2f() const = 0;   // phase-2 blocks of the fused step kernel
     // sample the Fermi-Dirac initial state into the state buffer
     virtual cudaError_t init_sample(cudaStream_t s) = 0;
     // histogram of the current state into hist buffer `buf` and moment partials into part1
@@ -60,9 +67,18 @@ public:
     // histogram of the current state into `hist` ([Q][Nk*Nk], zeroed by the caller) and moment
     // partials into `part` ([grid1()][Q*3]); touches no context buffer
     virtual cudaError_t observe_into(uint32_t *hist, double *part, cudaStream_t s) = 0;
-    // time step number `step` (histograms rotate over the three buffers); if ev is non-NULL,
-    // ev[0..2] are recorded before phase 1, between the phases and after phase 2
+    // time step number `step` as two launches on one stream; if ev is non-NULL, ev[0..3] are
+    // recorded before phase 1, after it, before phase 2 and after it
     virtual cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev = nullptr) = 0;
+    // the two launches of a step separately (phase 1 with a static tile assignment)
+    virtual cudaError_t phase1(int64_t n, bool out_step, cudaStream_t s) = 0;
+    virtual cudaError_t phase2(int64_t n, bool out_step, cudaStream_t s) = 0;
+    // pipelined form: one launch doing phase 1 of step n and phase 2 of step n - 1 with the
+    // continuation of its particles into step n (after phase1(n0) or a previous fused step)
+    virtual cudaError_t step_fused(int64_t n, bool out_n, bool out_prev, cudaStream_t s) = 0;
+    virtual bool fused() const = 0;   // step_fused is available for this shape
+    // copy the node tables to DevBuffers::tables (after the scratch buffer was cleared)
+    virtual cudaError_t upload_tables(cudaStream_t s) = 0;
     // histogram at one arbitrary z (psi of length P, FP64) into out [Nk*Nk]
     virtual cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) = 0;
 };
@@ -85,6 +101,9 @@ struct AdjBuffers;
 class AdjRunner;
 AdjRunner *make_adj_runner(int P, int Q, int precision, const HostTables &t, const DevBuffers &b, const AdjBuffers &ab,
                            int num_sms);
+
+// Bytes reserved for the device copy of the node tables (the largest compiled shape fits).
+constexpr size_t kTableBytes = 16384;
 
 // Launch accounting (every kernel launch of the library increments it).
 void count_launch(uint64_t n = 1);

@@ -39,6 +39,9 @@ public:
         args_.queue = b.queue;
         args_.part1 = b.part1;
         args_.part2 = b.part2;
+        args_.mark_words = b.mark_words;
+        static_assert(sizeof(Nodes<P, Q, R>) <= kTableBytes, "node tables exceed their device region");
+        args_.nd_dev = b.tables ? static_cast<const Nodes<P, Q, R> *>(b.tables) : nullptr;
         args_.counters = b.counters;
         args_.key0 = b.key0;
         args_.key1 = b.key1;
@@ -55,7 +58,8 @@ public:
         win_bytes_ = (size_t)Q * kWinWords * 4;
         args_.win_r0 = std::max(0, t.Nk / 2 - kWin / 2);
         bool win = t.Nk >= kWin && win_bytes_ <= 160 * 1024;
-        if (win && cudaFuncSetAttribute(k_phase1<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_) != cudaSuccess) {
+        if (win && (cudaFuncSetAttribute(k_phase1<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_) != cudaSuccess ||
+                    !fused_attr())) {
             cudaGetLastError();
             win = false;
         }
@@ -70,12 +74,15 @@ public:
         if (!win) win_bytes_ = 0;
         // phase 2: one resident wave (its work is one latency-bound collision chain per group)
         int per_sm2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_phase2<P, Q, R>, kPhase2Threads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_phase2<P, Q, R, true>, kPhase2Threads, 0);
         grid2_ = std::max(1, std::min(kGrid2, num_sms * std::max(per_sm2, 1)));
+        // the fused step kernel: as many collider groups as grid2_ blocks of phase 2 carry
+        grid2f_ = std::max(1, grid2_ * kPhase2Threads / kPhase1Threads);
     }
 
     int grid1() const override { return grid1_; }
     int grid2() const override { return grid2_; }
+    int grid2f() const override { return grid2f_; }
     const StepArgs<P, Q, R> &args() const { return args_; }
 
     cudaError_t init_sample(cudaStream_t s) override
@@ -107,24 +114,96 @@ public:
         return cudaGetLastError();
     }
 
-    cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev) override
+    // arguments of step n: buffer rotation (kHistBufs histograms, kQSlots counters, two queues
+    // and moment slots, kMarkSlots bitmaps)
+    StepArgs<P, Q, R> args_at(int64_t n) const
     {
         StepArgs<P, Q, R> a = args_;
-        const int cur = (int)(step % 3), nxt = (int)((step + 1) % 3), clr = (int)((step + 2) % 3);
-        a.Hcur = b_.hist + (int64_t)cur * b_.hist_stride;
-        a.Hnext = b_.hist + (int64_t)nxt * b_.hist_stride;
-        a.Hclear = b_.hist + (int64_t)clr * b_.hist_stride;
-        a.qcount = b_.qcount + (step & 1);
-        a.qcount_next = b_.qcount + ((step + 1) & 1);
-        a.step = (uint32_t)step;
+        auto H = [&](int64_t m) { return b_.hist + (int64_t)(m % kHistBufs) * b_.hist_stride; };
+        auto M = [&](int64_t m) { return b_.marks ? b_.marks + (int64_t)(m % kMarkSlots) * b_.mark_words : nullptr; };
+        a.Hcur = H(n);
+        a.Hnext = H(n + 1);
+        a.Hnext2 = H(n + 2);
+        a.Hclear = H(n + 2);
+        a.qcount = b_.qcount + (int)(n % kQSlots);
+        a.qcount_next = b_.qcount + (int)((n + 1) % kQSlots);
+        a.tilectr = nullptr;
+        a.tilectr_next = b_.qcount + 4 + (int)((n + 1) % kQSlots);
+        a.queue = b_.queue + (n & 1) * b_.queue_stride;
+        a.queue_next = b_.queue + ((n + 1) & 1) * b_.queue_stride;
+        a.mark = M(n);
+        a.mark_next = M(n + 1);
+        a.mark_clear = M(n + 1);
+        a.skip = nullptr;
+        a.part1 = b_.part1 + (n & 1) * b_.part1_stride;
+        a.partN = b_.partN ? b_.partN + ((n + 1) & 1) * (int64_t)kGrid2 * Q * 3 : nullptr;
+        a.step = (uint32_t)n;
+        return a;
+    }
+
+    cudaError_t phase1(int64_t n, bool out_step, cudaStream_t s) override
+    {
+        StepArgs<P, Q, R> a = args_at(n);
         a.out_step = out_step ? 1 : 0;
-        if (ev) cudaEventRecord(ev[0], s);
         k_phase1<P, Q, R><<<grid1_, kPhase1Threads, win_bytes_, s>>>(a);
-        if (ev) cudaEventRecord(ev[1], s);
-        k_phase2<P, Q, R><<<grid2_, kPhase2Threads, 0, s>>>(a);
-        if (ev) cudaEventRecord(ev[2], s);
-        count_launch(2);
+        count_launch();
         return cudaGetLastError();
+    }
+
+    cudaError_t phase2(int64_t n, bool out_step, cudaStream_t s) override
+    {
+        StepArgs<P, Q, R> a = args_at(n);
+        a.out_step = out_step ? 1 : 0;
+        k_phase2<P, Q, R, false><<<grid2_, kPhase2Threads, 0, s>>>(a);
+        count_launch();
+        return cudaGetLastError();
+    }
+
+    // the fused kernel takes two argument blocks: compiled for the shapes whose blocks fit the
+    // kernel-parameter space together (P * Q <= 64)
+    static constexpr bool kFused = P * Q <= 64;
+    bool fused() const override { return kFused; }
+
+    bool fused_attr()
+    {
+        if constexpr (kFused)
+            return cudaFuncSetAttribute(k_step<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_) == cudaSuccess;
+        return true;
+    }
+
+    cudaError_t step_fused(int64_t n, bool out_n, bool out_prev, cudaStream_t s) override
+    {
+        if constexpr (!kFused) {
+            (void)n; (void)out_n; (void)out_prev; (void)s;
+            return cudaErrorNotSupported;
+        } else {
+        if (!(b_.marks && b_.partN)) return cudaErrorInvalidValue;
+        StepArgs<P, Q, R> a1 = args_at(n), a2 = args_at(n - 1);
+        a1.out_step = out_n ? 1 : 0;
+        a1.skip = b_.marks + (int64_t)((n - 1) % kMarkSlots) * b_.mark_words;
+        a1.tilectr = b_.qcount + 4 + (int)(n % kQSlots);
+        a2.out_step = out_prev ? 1 : 0;
+        a2.out_next = out_n ? 1 : 0;
+        k_step<P, Q, R><<<grid2f_ + grid1_, kPhase1Threads, win_bytes_, s>>>(a1, a2, grid2f_);
+        count_launch();
+        return cudaGetLastError();
+        }
+    }
+
+    cudaError_t upload_tables(cudaStream_t s) override
+    {
+        if (!b_.tables) return cudaSuccess;
+        return cudaMemcpyAsync(b_.tables, &args_.nd, sizeof(Nodes<P, Q, R>), cudaMemcpyHostToDevice, s);
+    }
+
+    cudaError_t step(int64_t step, bool out_step, cudaStream_t s, cudaEvent_t *ev) override
+    {
+        if (ev) cudaEventRecord(ev[0], s);
+        cudaError_t e = phase1(step, out_step, s);
+        if (ev) { cudaEventRecord(ev[1], s); cudaEventRecord(ev[2], s); }
+        if (e == cudaSuccess) e = phase2(step, out_step, s);
+        if (ev) cudaEventRecord(ev[3], s);
+        return e;
     }
 
     cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) override
@@ -189,6 +268,7 @@ private:
     int grid1_ = 1;
     size_t win_bytes_ = 0;
     int grid2_ = 1;
+    int grid2f_ = 1;
 };
 
 template <int P, int Q>

@@ -62,6 +62,7 @@ SIGNATURES = {
                                   C.POINTER(C.c_size_t), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pgc_init": (C.c_int, [C.POINTER(pgc_config), _vp, _vp, _vp, _dp, _vp, C.POINTER(_vp)]),
     "pgc_step": (C.c_int, [_vp, C.c_int64, C.c_int32]),
+    "pgc_set_pipeline": (C.c_int, [_vp, C.c_int32]),
     "pgc_moments": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _i64p]),
     "pgc_reconstruct_f": (C.c_int, [_vp, _dp, C.c_int32, _u32p, _u32p]),
     "pgc_get_state": (C.c_int, [_vp, _dp]),
@@ -70,6 +71,7 @@ SIGNATURES = {
     "pgc_get_hist": (C.c_int, [_vp, _u32p, _u32p]),
     "pgc_profile": (C.c_int, [_vp, C.c_int32]),
     "pgc_profile_read": (C.c_int, [_vp, _dp, _dp, _i64p]),
+    "pgc_profile_timeline": (C.c_int, [_vp, _dp, C.c_int64, _i64p]),
     "pgc_observe_static": (C.c_int, [_vp, _vp, _vp, _vp]),
     "pgc_batch_query_sizes": (C.c_int, [C.POINTER(_vp), C.c_int32, C.POINTER(C.c_size_t)]),
     "pgc_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int32, _vp, C.c_int32, C.POINTER(_vp)]),
@@ -187,8 +189,20 @@ def pgc_get_hist(ctx, Q: int, Nk: int):
     return H, m
 
 
+def pgc_set_pipeline(ctx, on: bool):
+    _check(lib().pgc_set_pipeline(_vp(ctx), 1 if on else 0), _vp(ctx))
+
+
 def pgc_profile(ctx, every: int):
     _check(lib().pgc_profile(_vp(ctx), int(every)), _vp(ctx))
+
+
+def pgc_profile_timeline(ctx, max_samples: int = 4096):
+    """[n][4] ms: streaming-kernel start/end, collider-kernel start/end of each sampled step."""
+    t = np.zeros((max_samples, 4))
+    n = C.c_int64()
+    _check(lib().pgc_profile_timeline(_vp(ctx), _ptr(t, _dp), int(max_samples), C.byref(n)), _vp(ctx))
+    return t[: min(n.value, max_samples)]
 
 
 def pgc_profile_read(ctx):
@@ -340,6 +354,9 @@ class Simulation:
 
     def step(self, n_steps: int, moments_every: int = 0):
         pgc_step(self.ctx, n_steps, moments_every)
+
+    def set_pipeline(self, on: bool):
+        pgc_set_pipeline(self.ctx, on)
 
     def moments(self):
         return pgc_moments(self.ctx, self.Q, self.max_outputs)

@@ -54,7 +54,11 @@ def test_batch_cases_equal_standalone_runs(prec, use_graph):
         assert np.array_equal(sim.hist()[0], hs), p["stream_id"]
         mb = sim.moments()
         assert np.array_equal(mb["t_fs"], ms["t_fs"])
-        assert np.allclose(mb["nodes"], ms["nodes"], rtol=rtol, atol=0)
+        # FP32 warp sums grouped differently (batch tiles vs the pipelined standalone step):
+        # rounding ~1e-7 of the column's magnitude, which a near-zero column (V_y) shows as a
+        # large relative error
+        scale = np.abs(ms["nodes"]).max(axis=(0, 1), keepdims=True)
+        assert np.allclose(mb["nodes"], ms["nodes"], rtol=rtol, atol=(1e-13 if prec == "fp64" else 1e-6) * scale)
         cb = sim.counters()
         for k in ("attempts", "changed", "rejected", "capped", "steps"):
             assert cb[k] == cs[k], (k, cb[k], cs[k])
