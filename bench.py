@@ -379,7 +379,7 @@ def main():
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sim = pgc.Simulation(p, max_outputs=cap)
-    fused = sim.P * sim.Q <= 64           # pipelined form: one fused launch per time step
+    fused = sim.P * sim.Q <= 64           # pipelined form (the library default): one fused launch per time step
     sim.set_pipeline(fused)
     pgc.pgc_profile(sim.ctx, 10)
     stream = torch.cuda.current_stream(dev)

@@ -156,9 +156,9 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
  * forms; moment sums may differ in the last bits (FP32 summation order). */
 pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every);
 
-/* Switch the pipelined form of pgc_step on (1) or off (0).  Available and on by default when
- * P * Q <= 64; PGC_EUNSUPPORTED for larger shapes (for P = 21, Q = 36 the streaming work alone
- * fills the GPU). */
+/* Switch the pipelined form of pgc_step on (1) or off (0).  Available for every compiled shape
+ * and precision except P = 21, Q = 36 in FP64 (PGC_EUNSUPPORTED: the fused kernel's two argument
+ * blocks exceed the kernel-parameter space).  On by default when P * Q <= 64. */
 pgc_status pgc_set_pipeline(pgc_ctx *ctx, int32_t on);
 
 /* Copy the recorded time series to the host (synchronizes).  Any pointer may be NULL.

@@ -576,9 +576,10 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     ctx->tmp_max = (uint32_t *)(scr + L.off_tmpmax);
     ctx->rec_len = L.rec_len;
     ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
-    // the fused step overlaps the collider work with the streaming work; for the 36-node shape
-    // the streaming work alone fills the GPU
-    ctx->pipeline = ctx->run->fused() ? 1 : 0;
+    // the fused step overlaps the collider work with the streaming work.  For 36 nodes the
+    // collider work is itself throughput-bound (many chains per lane group) and, fused, holds
+    // most resident blocks for the whole launch: measured slower, so off by default there
+    ctx->pipeline = (ctx->run->fused() && L.P * L.Q <= 64) ? 1 : 0;
     if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
 
     cudaStream_t s = ctx->stream;

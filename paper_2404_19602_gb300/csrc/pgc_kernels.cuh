@@ -43,6 +43,11 @@ constexpr int kHistBufs = 4;
 constexpr int kQSlots = 3;
 constexpr int kMarkSlots = 3;
 
+// Basis of total degree <= 5 in two variables on 6 x 6 tensor nodes (the compiled 2-D shape):
+// coefficient (h1, h2) sits at index t(t+1)/2 + h2 with t = h1 + h2.
+template <int P, int Q> struct TensorShape { static constexpr bool value = (P == 21 && Q == 36); };
+__host__ __device__ constexpr int hidx2(int h1, int h2) { return (h1 + h2) * (h1 + h2 + 1) / 2 + h2; }
+
 // Quadrature / basis tables of one context (Sec. 4.1).
 template <int P, int Q, typename R>
 struct Nodes {
@@ -56,12 +61,12 @@ struct Nodes {
     // 2-D tensor nodes (P = 21, Q = 36): one-dimensional basis values for sum factorisation,
     // a1[q1][h1] = psi_h1(z1_q1), b2[q2][h2] = psi_h2(z2_q2)
     R a1[36], b2[36];
+    // FP32: the same weights as pairs (w, w), the operand of the two-lane FMA that reconstructs
+    // the x and y components together (unused in FP64)
+    unsigned long long psi2[TensorShape<P, Q>::value ? 1 : Q * P];
+    unsigned long long wpsi2[TensorShape<P, Q>::value ? 1 : Q * P];
+    unsigned long long a1_2[36], b2_2[36];
 };
-
-// Basis of total degree <= 5 in two variables on 6 x 6 tensor nodes (the compiled 2-D shape):
-// coefficient (h1, h2) sits at index t(t+1)/2 + h2 with t = h1 + h2.
-template <int P, int Q> struct TensorShape { static constexpr bool value = (P == 21 && Q == 36); };
-__host__ __device__ constexpr int hidx2(int h1, int h2) { return (h1 + h2) * (h1 + h2 + 1) / 2 + h2; }
 
 template <int P, int Q, typename R>
 struct StepArgs {
@@ -136,18 +141,42 @@ __device__ __forceinline__ void load_coeffs(const StepArgs<P, Q, R> &a, int64_t 
     }
 }
 
+// Two FP32 fused multiply-adds in one instruction (packed f32x2 of sm_100+; each lane rounds as
+// a scalar fmaf, so results are those of the scalar code): (x, y) pairs share a weight (w, w).
+struct F2 { unsigned long long v; };
+__device__ __forceinline__ F2 f2_pack(float a, float b)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 p, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.v)); }
+__device__ __forceinline__ F2 f2_fma(F2 a, unsigned long long w2, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(w2), "l"(c.v));
+    return r;
+}
+
 template <int P, int Q, typename R>
 __device__ __forceinline__ void recon_node(const Nodes<P, Q, R> &nd, int q, const R cx[P], const R cy[P],
                                            R &kx, R &ky)
 {
-    R sx = (R)0, sy = (R)0;
+    if constexpr (sizeof(R) == 4 && !TensorShape<P, Q>::value) {
+        F2 s = f2_pack(0.f, 0.f);
 #pragma unroll
-    for (int h = 0; h < P; ++h) {
-        sx += cx[h] * nd.psi[q * P + h];
-        sy += cy[h] * nd.psi[q * P + h];
+        for (int h = 0; h < P; ++h) s = f2_fma(f2_pack(cx[h], cy[h]), nd.psi2[q * P + h], s);
+        f2_unpack(s, kx, ky);
+    } else {
+        R sx = (R)0, sy = (R)0;
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            sx += cx[h] * nd.psi[q * P + h];
+            sy += cy[h] * nd.psi[q * P + h];
+        }
+        kx = sx;
+        ky = sy;
     }
-    kx = sx;
-    ky = sy;
 }
 
 // Reconstruction at every node (Eq. 23), calling f(q, kx, ky) per node.  For the 2-D tensor
@@ -156,7 +185,31 @@ __device__ __forceinline__ void recon_node(const Nodes<P, Q, R> &nd, int q, cons
 template <int P, int Q, typename R, typename F>
 __device__ __forceinline__ void recon_all(const Nodes<P, Q, R> &nd, const R cx[P], const R cy[P], F &&f)
 {
-    if constexpr (TensorShape<P, Q>::value) {
+    if constexpr (TensorShape<P, Q>::value && sizeof(R) == 4) {
+        F2 c2[P];
+#pragma unroll
+        for (int h = 0; h < P; ++h) c2[h] = f2_pack(cx[h], cy[h]);
+#pragma unroll
+        for (int q1 = 0; q1 < 6; ++q1) {
+            F2 t2[6];
+#pragma unroll
+            for (int h2 = 0; h2 < 6; ++h2) {
+                F2 s2 = f2_pack(0.f, 0.f);
+#pragma unroll
+                for (int h1 = 0; h1 + h2 <= 5; ++h1) s2 = f2_fma(c2[hidx2(h1, h2)], nd.a1_2[q1 * 6 + h1], s2);
+                t2[h2] = s2;
+            }
+#pragma unroll
+            for (int q2 = 0; q2 < 6; ++q2) {
+                F2 k2 = f2_pack(0.f, 0.f);
+#pragma unroll
+                for (int h2 = 0; h2 < 6; ++h2) k2 = f2_fma(t2[h2], nd.b2_2[q2 * 6 + h2], k2);
+                R kx, ky;
+                f2_unpack(k2, kx, ky);
+                f(q1 * 6 + q2, kx, ky);
+            }
+        }
+    } else if constexpr (TensorShape<P, Q>::value) {
 #pragma unroll
         for (int q1 = 0; q1 < 6; ++q1) {
             R tx[6], ty[6];
@@ -617,12 +670,22 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
 #pragma unroll (P * Q <= 64 ? P : 1)
         for (int h = 0; h < P; ++h) {
             R sx = (R)0, sy = (R)0;
+            if constexpr (sizeof(R) == 4 && !TensorShape<P, Q>::value) {
+                F2 s2 = f2_pack(0.f, 0.f);
 #pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) {
-                    sx += nd.wpsi[q * P + h] * kx[s];
-                    sy += nd.wpsi[q * P + h] * ky[s];
+                for (int s = 0; s < NPL; ++s) {
+                    const int q = r + s * G;
+                    if (q < Q) s2 = f2_fma(f2_pack(kx[s], ky[s]), nd.wpsi2[q * P + h], s2);
+                }
+                f2_unpack(s2, sx, sy);
+            } else {
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const int q = r + s * G;
+                    if (q < Q) {
+                        sx += nd.wpsi[q * P + h] * kx[s];
+                        sy += nd.wpsi[q * P + h] * ky[s];
+                    }
                 }
             }
             cx[h] = group_sum<G>(sx, gmask);

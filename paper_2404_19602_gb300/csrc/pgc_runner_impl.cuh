@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "pgc_kernels.cuh"
 #include "pgc_runner.h"
@@ -31,6 +32,16 @@ public:
                 }
         }
         nd.drift_mask = t.drift_mask;
+        // (w, w) pairs of the FP32 weights for the two-lane FMA
+        auto pair = [](double w) {
+            const float f = (float)w;
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            return ((unsigned long long)u << 32) | u;
+        };
+        if constexpr (!TensorShape<P, Q>::value)
+            for (int i = 0; i < Q * P; ++i) { nd.psi2[i] = pair(t.psi[i]); nd.wpsi2[i] = pair(t.wpsi[i]); }
+        for (int i = 0; i < 36; ++i) { nd.a1_2[i] = pair((double)nd.a1[i]); nd.b2_2[i] = pair((double)nd.b2[i]); }
         args_.khat = static_cast<R *>(b.state);
         args_.N = b.N;
         args_.ld = b.ld;
@@ -159,9 +170,9 @@ public:
         return cudaGetLastError();
     }
 
-    // the fused kernel takes two argument blocks: compiled for the shapes whose blocks fit the
-    // kernel-parameter space together (P * Q <= 64)
-    static constexpr bool kFused = P * Q <= 64;
+    // the fused kernel takes two argument blocks: compiled where both fit the kernel-parameter
+    // space (32764 bytes; all shapes but the 36-node FP64 one)
+    static constexpr bool kFused = 2 * sizeof(StepArgs<P, Q, R>) + sizeof(int) <= 32764;
     bool fused() const override { return kFused; }
 
     bool fused_attr()

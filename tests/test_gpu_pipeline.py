@@ -50,6 +50,7 @@ CASES = [
     ("gap_fp32", W.scaled(W.GAP_UQ_1E6, N=50001), [2, 37, 1, 20], 10, 2e-5),
     ("gap_fp64", W.scaled(W.GAP_UQ_1E6, N=20000, precision="fp64"), [30], 1, 1e-12),
     ("gap_current_max_fp32", W.scaled(W.GAP_UQ_1E6, N=40000, pauli_norm=1), [31], 10, 2e-5),
+    ("gap_field_fp32", W.scaled(W.GAP_FIELD_UQ_4E6, N=30001), [25, 3], 7, 2e-5),
 ]
 
 
@@ -76,10 +77,11 @@ def test_pipeline_switch_between_calls():
     _compare(got, ref, 2e-5)
 
 
-def test_pipeline_unavailable_for_36_nodes():
+def test_pipeline_unavailable_for_36_nodes_fp64():
+    """The fused kernel's two argument blocks exceed the parameter space for P = 21, Q = 36 in FP64."""
     from paper_2404_19602_gb300 import pgc
 
-    s = pgc.Simulation(W.scaled(W.GAP_FIELD_UQ_4E6, N=1000), max_outputs=4)
+    s = pgc.Simulation(W.scaled(W.GAP_FIELD_UQ_4E6, N=1000, precision="fp64"), max_outputs=4)
     with pytest.raises(pgc.PgcError):
         s.set_pipeline(True)
     s.set_pipeline(False)
