@@ -33,7 +33,8 @@ if ROOT not in sys.path:
 from paper_2404_19602_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None,
-             "adjoint": W.ADJOINT_1E6}
+             "adjoint": W.ADJOINT_1E6,
+             "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64")}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -49,7 +50,8 @@ def parse():
     ap.add_argument("--workload", default="gap_uq", choices=sorted(WORKLOADS),
                     help="gap_uq (1e6 particles, 1 random input), det (1e4, FP64), gap_field (4e6, 2 random "
                          "inputs), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
-                         "reverse sweep of the steady-current sensitivities, 1e6 particles)")
+                         "reverse sweep of the steady-current sensitivities, 1e6 particles), gap_uq_fp64 "
+                         "(the gap_uq ensemble in the FP64 mode)")
     ap.add_argument("--fd-check", action="store_true",
                     help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")

@@ -203,7 +203,7 @@ __device__ __forceinline__ R rate_bound(const Phys<R> &ph, R eps, R eps0max)
 // Both maps are monotone; bisection to the working precision.
 // ------------------------------------------------------------------------------------------
 template <typename R>
-__device__ R solve_angle(R u, R sgn)
+__device__ __noinline__ R solve_angle(R u, R sgn)
 {
     // f(th) = th + sgn sin th - 2 pi u is non-decreasing on [0, 2pi]; safeguarded Newton from a
     // start that captures the cubic behaviour at the stationary point (th = pi for sgn = +1,

@@ -620,22 +620,23 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
     }
     R gc[NPL][6];  // rates of the current state at the lane's nodes (reused by the selection)
-    auto majorant = [&]() {
+    R tc = (R)0;
+    uint32_t c = 0;
+    bool touched = false;
+    // One pass per free flight: majorant of the current state (Eq. (25)), flight time, and, if
+    // the flight ends inside the step, a collision.  The rates and the random draw have one
+    // call site each (instruction-cache footprint).
+    for (;;) {
         R gm = (R)0;
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
             if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
         }
-        return ph.alpha1 * group_max<G>(gm, gmask);
-    };
-    R Gt = majorant();
-    R tc = (R)0;
-    uint32_t c = 0;
-    U4 rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
-    R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
-    bool touched = false;
-    while (tc + dtc < ph.dt) {               // group-uniform condition
+        const R Gt = ph.alpha1 * group_max<G>(gm, gmask);
+        const U4 rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
+        const R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
+        if (!(tc + dtc < ph.dt)) break;             // group-uniform condition
         if ((int)c >= ph.max_coll) { if (r == 0) ++cnt.cap; break; }
         if (r == 0) ++cnt.att;
         touched = true;
@@ -696,11 +697,8 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             const int q = r + s * G;
             if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
         }
-        Gt = majorant();
         tc += dtc;
         ++c;
-        rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
-        dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
     }
     if constexpr (EXT) {
         // drift of step n + 1 (before the store: the stored state is the post-drift one, as phase 1 leaves it)
@@ -842,7 +840,7 @@ __device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid
 }
 
 template <int P, int Q, typename R, bool EXT>
-__global__ void __launch_bounds__(kPhase2Threads, (P * Q > 64) ? 3 : 4)
+__global__ void __launch_bounds__(kPhase2Threads, 4)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
     phase2_block<P, Q, R, EXT>(a, blockIdx.x, gridDim.x);
