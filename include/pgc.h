@@ -85,6 +85,11 @@ enum {
 enum { PGC_FP32 = 0, PGC_FP64 = 1 };
 enum { PGC_PAULI_INITIAL_MAX = 0, PGC_PAULI_CURRENT_MAX = 1, PGC_PAULI_OFF = 2 };
 enum { PGC_FS_PAPER = 0, PGC_FS_EXACT_ENERGY = 1 };
+/* How the band minimum depends on z (Sec. 2: eps0 = hbar vF pi / W, W the ribbon width):
+ * AFFINE: eps0(z) affine between eps0_eV.lo and .hi; WIDTH: the width is the input, W(z) affine
+ * between width_nm.lo and .hi and eps0(z) = hbar vF pi / W(z) (not a polynomial in z; the
+ * scenario of Test 2, W = (6.5 + z) nm). */
+enum { PGC_EPS0_AFFINE = 0, PGC_EPS0_WIDTH = 1 };
 
 /* counters returned by pgc_counters */
 enum {
@@ -104,7 +109,7 @@ typedef struct { double lo, hi; } pgc_interval;  /* lo == hi: deterministic inpu
 typedef struct {
     double T_K;              /* lattice and initial Fermi-Dirac temperature (300) */
     double eps_F_eV;         /* Fermi level of the initial state (0.4) */
-    pgc_interval eps0_eV;    /* conduction-band minimum hbar vF pi / W; band gap E_g = 2 eps0 */
+    pgc_interval eps0_eV;    /* conduction-band minimum hbar vF pi / W; band gap E_g = 2 eps0 (AFFINE law) */
     pgc_interval Ex_Vcm;     /* field along x; E_y = 0 */
     uint32_t mech_mask;      /* PGC_MECH_*; 0 = ballistic */
     double alpha;            /* self-scattering tuning of Eq. (19) (0.1) */
@@ -122,6 +127,8 @@ typedef struct {
     int32_t n_theta_edge;    /* trapezoid points of the edge integral (64; even, 4..256) */
     int32_t max_collisions;  /* per particle and step (32) */
     int32_t max_outputs;     /* capacity of the moment time series */
+    int32_t eps0_law;        /* PGC_EPS0_AFFINE (default) or PGC_EPS0_WIDTH */
+    pgc_interval width_nm;   /* ribbon width, nm (WIDTH law; lo > 0) */
 } pgc_config;
 
 typedef struct pgc_ctx pgc_ctx;
@@ -274,6 +281,8 @@ const char *pgc_batch_last_error(const pgc_batch *b);
 /* backwards (transposed Jacobians of drift, reconstruction, final-state maps and projection,  */
 /* moment terms), ending with the sensitivity of the Fermi-Dirac sampling.                     */
 /* Work memory (caller-owned device buffer) from pgc_adjoint_query_sizes.                      */
+/* PGC_EUNSUPPORTED for the WIDTH band-minimum law, the exact-energy final states and the      */
+/* current-maximum Pauli normalisation.                                                       */
 /* Supported: the paper's final states; Pauli initial-maximum or off.                          */
 /* ---------------------------------------------------------------------------------------- */
 pgc_status pgc_adjoint_query_sizes(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, size_t *work_bytes);

@@ -58,6 +58,7 @@ class _Cfg(C.Structure):
         ("seed", C.c_uint64), ("stream_id", C.c_uint32),
         ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
         ("n_theta", C.c_int32), ("max_coll", C.c_int32),
+        ("eps0_law", C.c_int32), ("W_lo", C.c_double), ("W_hi", C.c_double),
     ]
 
 
@@ -129,7 +130,7 @@ def _u32p(a):
 DEFAULTS = dict(T_K=300.0, eps_F=0.4, eps0_lo=0.1, eps0_hi=0.1, Ex_lo=5000.0, Ex_hi=5000.0,
                 mech_mask=ALL_MECH, alpha=0.1, Nk=240, Lk_hvF=5.0, M=5, Q1=6, N=1000,
                 dt_fs=1.0, seed=1, stream_id=0, pauli_norm=PAULI_INITIAL_MAX,
-                final_state=FS_PAPER, n_theta=64, max_coll=32)
+                final_state=FS_PAPER, n_theta=64, max_coll=32, eps0_law=0, W_lo=0.0, W_hi=0.0)
 
 
 def make_cfg(params: dict) -> _Cfg:
@@ -137,6 +138,9 @@ def make_cfg(params: dict) -> _Cfg:
     for k, v in params.items():
         if k in p:
             p[k] = v
+    if (params.get("W_lo") or 0.0) > 0.0:   # the width is the input: eps0 = pi hbar vF / W
+        p["eps0_law"] = 1
+        p["W_hi"] = params.get("W_hi", params["W_lo"])
     c = _Cfg()
     for k, v in p.items():
         setattr(c, k, v)

@@ -74,6 +74,10 @@
 /* final-state readings for OP/K */
 #define ORC_FS_PAPER 0
 #define ORC_FS_EXACT_ENERGY 1
+/* how the band minimum depends on z: directly (an interval of eps0), or through the ribbon
+   width, eps0 = pi hbar vF / W (Sec. 2), with W spread over an interval (Test 2) */
+#define ORC_EPS0_AFFINE 0
+#define ORC_EPS0_WIDTH 1
 
 typedef struct {
     double T_K;               /* lattice = initial Fermi-Dirac temperature */
@@ -94,6 +98,8 @@ typedef struct {
     int32_t final_state;      /* ORC_FS_* */
     int32_t n_theta;          /* trapezoid points of the edge integral (Appendix A) */
     int32_t max_coll;         /* safety cap of collisions per particle and step */
+    int32_t eps0_law;         /* ORC_EPS0_AFFINE or ORC_EPS0_WIDTH */
+    double W_lo, W_hi;        /* ribbon width interval, nm (ORC_EPS0_WIDTH) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -272,10 +278,30 @@ static void legendre_on(int M, double z, double *out)
     }
 }
 
+/* is the band minimum uncertain? (its own interval, or the width's) */
+static int orc_eps_random(const orc_cfg *c)
+{
+    if (c->eps0_law == ORC_EPS0_WIDTH) return c->W_lo != c->W_hi;
+    return c->eps0_lo != c->eps0_hi;
+}
+
+/* band minimum for the band-minimum variable z1 in [-1,1] (z ~ U maps affinely onto the
+   interval of the uncertain quantity); with the width law the affine quantity is W and
+   eps0 = pi hbar vF / W, the lowest transverse subband of a ribbon of width W (Sec. 2) */
+static double orc_band_min(const orc_cfg *c, double hvF, double z1)
+{
+    int rnd = orc_eps_random(c);
+    if (c->eps0_law == ORC_EPS0_WIDTH) {
+        double W = rnd ? c->W_lo + 0.5 * (c->W_hi - c->W_lo) * (z1 + 1.0) : c->W_lo;
+        return ORC_PI * hvF / W;
+    }
+    return rnd ? c->eps0_lo + 0.5 * (c->eps0_hi - c->eps0_lo) * (z1 + 1.0) : c->eps0_lo;
+}
+
 /* number of random dimensions, basis size P, node count Q */
 static int orc_dims(const orc_cfg *c, int *P, int *Q)
 {
-    int d = (c->eps0_lo != c->eps0_hi) + (c->Ex_lo != c->Ex_hi);
+    int d = orc_eps_random(c) + (c->Ex_lo != c->Ex_hi);
     if (d == 0) { *P = 1; *Q = 1; }
     else if (d == 1) { *P = c->M + 1; *Q = c->Q1; }
     else { *P = (c->M + 1) * (c->M + 2) / 2; *Q = c->Q1 * c->Q1; }
@@ -506,11 +532,11 @@ void *orc_create(const orc_cfg *cfg)
     }
     for (int q = 0; q < Q; ++q) {
         double z1 = 0.0, z2 = 0.0;
-        int eps_random = (cfg->eps0_lo != cfg->eps0_hi), E_random = (cfg->Ex_lo != cfg->Ex_hi);
+        int eps_random = orc_eps_random(cfg), E_random = (cfg->Ex_lo != cfg->Ex_hi);
         if (d == 1) { if (eps_random) z1 = S->zq[q]; else z2 = S->zq[q]; }
         if (d == 2) { z1 = S->zq[2 * q]; z2 = S->zq[2 * q + 1]; }
-        /* affine maps of z in [-1,1] onto the parameter intervals (z ~ U) */
-        S->eps0q[q] = eps_random ? cfg->eps0_lo + 0.5 * (cfg->eps0_hi - cfg->eps0_lo) * (z1 + 1.0) : cfg->eps0_lo;
+        /* maps of z in [-1,1] onto the parameters (z ~ U) */
+        S->eps0q[q] = orc_band_min(cfg, S->hvF, z1);
         S->Exq[q] = E_random ? cfg->Ex_lo + 0.5 * (cfg->Ex_hi - cfg->Ex_lo) * (z2 + 1.0) : cfg->Ex_lo;
         /* drift of Eq. (17): (e/hbar) E dt, E in V/cm -> eV/nm is 1e-7 */
         S->dq[q] = S->Exq[q] * 1e-7 * cfg->dt_fs / S->hbar_fs;
@@ -1025,9 +1051,9 @@ void orc_observe_at(const void *st, const double *z, double *out4)
     double psi[1296];
     orc_psi_at(c, (S->d > 0) ? z : NULL, psi);
     double z1 = 0.0;
-    if (S->d == 1 && c->eps0_lo != c->eps0_hi) z1 = z[0];
+    if (S->d == 1 && orc_eps_random(c)) z1 = z[0];
     if (S->d == 2) z1 = z[0];
-    double e0 = (c->eps0_lo != c->eps0_hi) ? c->eps0_lo + 0.5 * (c->eps0_hi - c->eps0_lo) * (z1 + 1.0) : c->eps0_lo;
+    double e0 = orc_band_min(c, S->hvF, z1);
     double svx = 0.0, svy = 0.0, se = 0.0;
     for (int64_t i = 0; i < N; ++i) {
         double kx = 0.0, ky = 0.0;
@@ -1072,7 +1098,7 @@ int orc_num_threads(void)
 static void node_param_derivs(const orc_state *S, int q, double de0[NTH], double dE[NTH])
 {
     const orc_cfg *c = &S->cfg;
-    int eps_random = (c->eps0_lo != c->eps0_hi), E_random = (c->Ex_lo != c->Ex_hi);
+    int eps_random = orc_eps_random(c), E_random = (c->Ex_lo != c->Ex_hi);
     double z1 = 0.0, z2 = 0.0;
     if (S->d == 1) { if (eps_random) z1 = S->zq[q]; else z2 = S->zq[q]; }
     if (S->d == 2) { z1 = S->zq[2 * q]; z2 = S->zq[2 * q + 1]; }

@@ -121,9 +121,26 @@ static void basis_at(int d, int M, const double *z, double *psi)
         for (int j = 0; j <= t; ++j) psi[h++] = a[t - j] * b[j];
 }
 
+// Is the band minimum a random input (per its law)?
+static bool eps_random_of(const pgc_config &c)
+{
+    return c.eps0_law == PGC_EPS0_WIDTH ? c.width_nm.lo != c.width_nm.hi : c.eps0_eV.lo != c.eps0_eV.hi;
+}
+
+// Band minimum at the band-minimum variable z in [-1,1] (eps0 = hbar vF pi / W, Sec. 2).
+static double eps0_at(const pgc_config &c, double hvF, double z)
+{
+    const bool er = eps_random_of(c);
+    if (c.eps0_law == PGC_EPS0_WIDTH) {
+        const double W = er ? c.width_nm.lo + 0.5 * (c.width_nm.hi - c.width_nm.lo) * (z + 1.0) : c.width_nm.lo;
+        return kPi * hvF / W;
+    }
+    return er ? c.eps0_eV.lo + 0.5 * (c.eps0_eV.hi - c.eps0_eV.lo) * (z + 1.0) : c.eps0_eV.lo;
+}
+
 static int dims_of(const pgc_config &c, int *P, int *Q)
 {
-    const bool er = c.eps0_eV.lo != c.eps0_eV.hi, fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
+    const bool er = eps_random_of(c), fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
     const int d = (int)er + (int)fr;
     if (d == 0) { *P = 1; *Q = 1; }
     else if (d == 1) { *P = c.degree_M + 1; *Q = c.quad_per_dim; }
@@ -194,7 +211,7 @@ static void build_tables(const pgc_config &c, HostTables &t)
                     t.w[q] = w1[q1] * w1[q2];
                 }
     }
-    const bool er = c.eps0_eV.lo != c.eps0_eV.hi, fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
+    const bool er = eps_random_of(c), fr = c.Ex_Vcm.lo != c.Ex_Vcm.hi;
     t.eps_random = er;
     t.field_random = fr;
     t.psi.assign((size_t)Q * P, 0.0);
@@ -205,7 +222,7 @@ static void build_tables(const pgc_config &c, HostTables &t)
         double ze = 0.0, zf = 0.0;
         if (d == 1) { if (er) ze = t.z[q]; else zf = t.z[q]; }
         if (d == 2) { ze = t.z[2 * q]; zf = t.z[2 * q + 1]; }
-        t.eps0[q] = er ? c.eps0_eV.lo + 0.5 * (c.eps0_eV.hi - c.eps0_eV.lo) * (ze + 1.0) : c.eps0_eV.lo;
+        t.eps0[q] = eps0_at(c, t.hvF, ze);
         t.Ex[q] = fr ? c.Ex_Vcm.lo + 0.5 * (c.Ex_Vcm.hi - c.Ex_Vcm.lo) * (zf + 1.0) : c.Ex_Vcm.lo;
         t.dq[q] = t.Ex[q] * 1.0e-7 * c.dt_fs / t.hbar_fs;
         t.nq[q] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper<double>(t.eps0[q], c.eps_F_eV, kT) * 1.0e18;
@@ -400,7 +417,11 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     if (!c) { *msg = "cfg is NULL"; return PGC_EINVAL; }
     auto bad = [&](const char *m) { *msg = m; return PGC_EINVAL; };
     if (!(c->T_K > 0.0)) return bad("T_K must be > 0");
-    if (!(c->eps0_eV.lo > 0.0) || !(c->eps0_eV.hi >= c->eps0_eV.lo)) return bad("eps0 interval must satisfy 0 < lo <= hi");
+    if (c->eps0_law != PGC_EPS0_AFFINE && c->eps0_law != PGC_EPS0_WIDTH) return bad("eps0_law must be PGC_EPS0_AFFINE or PGC_EPS0_WIDTH");
+    if (c->eps0_law == PGC_EPS0_AFFINE && (!(c->eps0_eV.lo > 0.0) || !(c->eps0_eV.hi >= c->eps0_eV.lo)))
+        return bad("eps0 interval must satisfy 0 < lo <= hi");
+    if (c->eps0_law == PGC_EPS0_WIDTH && (!(c->width_nm.lo > 0.0) || !(c->width_nm.hi >= c->width_nm.lo) || !std::isfinite(c->width_nm.hi)))
+        return bad("width interval must satisfy 0 < lo <= hi (finite)");
     if (!(c->Ex_Vcm.hi >= c->Ex_Vcm.lo) || !std::isfinite(c->Ex_Vcm.lo) || !std::isfinite(c->Ex_Vcm.hi))
         return bad("Ex interval must satisfy lo <= hi (finite)");
     if (c->mech_mask > 63u) return bad("mech_mask has unknown bits");
@@ -477,6 +498,8 @@ void pgc_config_default(pgc_config *c)
     c->n_theta_edge = 64;
     c->max_collisions = 32;
     c->max_outputs = 1024;
+    c->eps0_law = PGC_EPS0_AFFINE;
+    c->width_nm.lo = c->width_nm.hi = 0.0;
 }
 
 pgc_status pgc_query_sizes(const pgc_config *cfg, size_t *state_bytes, size_t *hist_bytes,

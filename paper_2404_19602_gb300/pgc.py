@@ -49,7 +49,11 @@ class pgc_config(C.Structure):
         ("seed", C.c_uint64), ("stream_id", C.c_uint32),
         ("precision", C.c_int32), ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
         ("n_theta_edge", C.c_int32), ("max_collisions", C.c_int32), ("max_outputs", C.c_int32),
+        ("eps0_law", C.c_int32), ("width_nm", pgc_interval),
     ]
+
+
+PGC_EPS0_AFFINE, PGC_EPS0_WIDTH = 0, 1
 
 
 _vp, _dp, _u32p, _u64p, _i64p = (C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
@@ -308,6 +312,10 @@ def config_from(params: dict, max_outputs: int = 1024) -> pgc_config:
     c.n_theta_edge = p.get("n_theta", c.n_theta_edge)
     c.max_collisions = p.get("max_coll", c.max_collisions)
     c.max_outputs = max_outputs
+    if (p.get("W_lo") or 0.0) > 0.0:   # width law: eps0(z) = hbar vF pi / W(z), W affine in z
+        c.eps0_law = PGC_EPS0_WIDTH
+        c.width_nm.lo = p["W_lo"]
+        c.width_nm.hi = p.get("W_hi", p["W_lo"])
     return c
 
 

@@ -12,6 +12,8 @@ random dimension), N (particles), dt_fs, seed (Philox key), stream_id, pauli_nor
 paper's |k| -+ omega/vF, 1 = exact energy), n_theta (trapezoid points of the edge integral).
 
 A band gap E_g maps to eps0 = E_g / 2 (the conduction-band minimum of the gapped Dirac cone).
+With W_lo/W_hi (nm) present the ribbon width is the input instead: W(z) spreads affinely over
+[W_lo, W_hi] and eps0(z) = pi hbar vF / W(z) (eps0_lo/eps0_hi are then unused).
 """
 from __future__ import annotations
 
@@ -46,6 +48,19 @@ GAP_FIELD_UQ_4E6 = _w(name="gapU[0.1,0.3]eV_fieldU[1,10]kVcm_M5_Q36_N4e6_fp32", 
 ADJOINT_1E6 = _w(name="adjoint_gapU[0.1,0.3]eV_5kVcm_M5_N1e6", eps0_lo=0.05, eps0_hi=0.15,
                  Ex_lo=5000.0, Ex_hi=5000.0, M=5, Q1=6, N=1_000_000, dt_fs=1.0, steps=5000,
                  ckpt_every=250, steady_window=250, precision="fp32")
+
+
+#: Test 2 (Sec. 5), first scenario: uncertain ribbon width W = (6.5 + z) nm, z ~ U[0,1] (the band
+#: minimum pi hbar vF / W(z) is not a polynomial in z), deterministic field 0.5 V/um, eps_F 0.4 eV,
+#: dt 2.5 fs, 3 ps, 1e6 particles, M = 5.
+TEST2_WIDTH_1E6 = _w(name="test2_W6.5-7.5nm_E5kVcm_epsF0.4_M5_N1e6_fp32", W_lo=6.5, W_hi=7.5,
+                     Ex_lo=5000.0, Ex_hi=5000.0, M=5, Q1=6, N=1_000_000, dt_fs=2.5, steps=1200,
+                     precision="fp32")
+
+#: Test 2, second scenario: uncertain field E = (0.4 + 0.2 z) V/um, width 7 nm.
+TEST2_FIELD_1E6 = _w(name="test2_W7nm_E4-6kVcm_epsF0.4_M5_N1e6_fp32", W_lo=7.0, W_hi=7.0,
+                     Ex_lo=4000.0, Ex_hi=6000.0, M=5, Q1=6, N=1_000_000, dt_fs=2.5, steps=1200,
+                     precision="fp32")
 
 
 def sweep64(seed: int = 1, n_lo: float = 1e5, n_hi: float = 4e6, steps: int = 3000):

@@ -162,6 +162,31 @@ def test_gap_field_uq_fp32_moments():
     _compare_moments(sim.moments(), o.moments(), 1e-3)
 
 
+def test_width_law_fp64_elementwise():
+    """Test 2, uncertain ribbon width W = (6.5 + z) nm: the band minimum pi hbar vF / W(z) at the
+    nodes, dt = 2.5 fs; FP64 trajectories follow the oracle's."""
+    p = W.scaled(W.TEST2_WIDTH_1E6, N=5000, precision="fp64")
+    sim, o = _run_pair(p, 120, 10)
+    worst = _compare_moments(sim.moments(), o.moments(), 1e-3)
+    assert worst <= 1e-8, worst
+    g, r = sim.state(), o.state()
+    diverged = (np.abs(g - r).max(axis=(0, 1)) > 1e-8).sum()
+    assert diverged <= 2, diverged
+
+
+def test_width_law_fp32_moments():
+    p = W.scaled(W.TEST2_WIDTH_1E6, N=20000)
+    sim, o = _run_pair(p, 30, 10)
+    _compare_moments(sim.moments(), o.moments(), 1e-3)
+
+
+def test_test2_field_scenario_fp32_moments():
+    """Test 2, uncertain field E = (0.4 + 0.2 z) V/um at a deterministic width of 7 nm."""
+    p = W.scaled(W.TEST2_FIELD_1E6, N=20000)
+    sim, o = _run_pair(p, 30, 10)
+    _compare_moments(sim.moments(), o.moments(), 1e-3)
+
+
 @pytest.mark.parametrize("N", [1, 33, 257, 65 * 64 + 3])
 def test_ragged_sizes_fp64(N):
     p = W.scaled(W.GAP_UQ_1E6, N=N, precision="fp64")
