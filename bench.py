@@ -383,7 +383,7 @@ def main():
     sim = pgc.Simulation(p, max_outputs=cap)
     fused = sim.P * sim.Q <= 64           # pipelined form (the library default): one fused launch per time step
     sim.set_pipeline(fused)
-    pgc.pgc_profile(sim.ctx, 10)
+    pgc.pgc_profile(sim.ctx, 50)                # kernel timing samples: every 50th time step
     stream = torch.cuda.current_stream(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler(local)

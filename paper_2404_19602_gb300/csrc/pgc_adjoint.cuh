@@ -259,7 +259,7 @@ template <int P, int Q, typename R>
 __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const AdjArgs<P, Q, R> &a,
                                               int64_t i, int r, unsigned gmask, int stop, R cx[P], R cy[P],
                                               R kx[GroupOf<Q>::NPL], R ky[GroupOf<Q>::NPL], int *nev,
-                                              int l_out[GroupOf<Q>::NPL], U4 *r_out)
+                                              int l_out[GroupOf<Q>::NPL], U4 *r_out, R *red)
 {
     constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
     const int64_t NN = (int64_t)ph.Nk * ph.Nk;
@@ -352,20 +352,7 @@ __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, 
             }
             if (accept) { kx[s] = nkx; ky[s] = nky; }
         }
-#pragma unroll
-        for (int h = 0; h < P; ++h) {
-            R sx = (R)0, sy = (R)0;
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) {
-                    sx += nd.wpsi[q * P + h] * kx[s];
-                    sy += nd.wpsi[q * P + h] * ky[s];
-                }
-            }
-            cx[h] = group_sum<G>(sx, gmask);
-            cy[h] = group_sum<G>(sy, gmask);
-        }
+        project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, red);   // the forward's projection
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
@@ -388,6 +375,7 @@ k_adj_collide(const __grid_constant__ AdjArgs<P, Q, R> a)
     constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
     __shared__ __align__(16) uint32_t sph[(sizeof(Phys<R>) + 3) / 4];
     __shared__ __align__(16) uint32_t snd[(sizeof(Nodes<P, Q, R>) + 3) / 4];
+    __shared__ R sred[ProjRed<P, Q, R>::value ? (kPhase2Threads / 32) * ProjRed<P, Q, R>::warp_elems : 1];
     stage(sph, a.ph);
     stage(snd, a.nd);
     __syncthreads();
@@ -411,10 +399,10 @@ k_adj_collide(const __grid_constant__ AdjArgs<P, Q, R> a)
         R cx[P], cy[P], kx[NPL], ky[NPL];
         int nev = 0, lsel[NPL];
         U4 rr;
-        replay_events(ph, nd, a, i, r, gmask, 1 << 30, cx, cy, kx, ky, &nev, lsel, &rr);
+        replay_events(ph, nd, a, i, r, gmask, 1 << 30, cx, cy, kx, ky, &nev, lsel, &rr, sred);
         for (int e = nev - 1; e >= 0; --e) {
             int dummy;
-            replay_events(ph, nd, a, i, r, gmask, e, cx, cy, kx, ky, &dummy, lsel, &rr);
+            replay_events(ph, nd, a, i, r, gmask, e, cx, cy, kx, ky, &dummy, lsel, &rr, sred);
             EventAngles<R> ang;
             ang.reset(u01<R>(rr.w));
             // lambda_e = sum_q Psi_q^T J_q^T (W_q^T lambda_{e+1})

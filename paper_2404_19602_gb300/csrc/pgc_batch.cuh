@@ -147,6 +147,7 @@ k_phase2_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
     constexpr int G = GroupOf<Q>::G;
     __shared__ int64_t sbase[kBatchMaxCases + 1];
     __shared__ uint32_t scnt[kBatchMaxCases][5];   // per-case counters of this block
+    __shared__ R sred[ProjRed<P, Q, R>::value ? (kPhase2Threads / 32) * ProjRed<P, Q, R>::warp_elems : 1];
     for (int j = threadIdx.x; j <= a.ncases; j += blockDim.x) sbase[j] = a.bases[j];
     for (int j = threadIdx.x; j < a.ncases * 5; j += blockDim.x) (&scnt[0][0])[j] = 0u;
     __syncthreads();
@@ -173,6 +174,7 @@ k_phase2_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
         t.mom = a.part2c + (int64_t)c * (Q * 3);
         t.key0 = cd.key0; t.key1 = cd.key1; t.stream_id = cd.stream_id; t.step = (uint32_t)step;
         t.out_step = out;
+        t.red = sred;
         P2Counts cnt;
         collide_particle<P, Q, R>(ph, cd.nd, t, g - sbase[c], r, gmask, cnt);
         if (cnt.att) atomicAdd(&scnt[c][0], (uint32_t)cnt.att);

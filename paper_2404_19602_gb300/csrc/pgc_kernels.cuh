@@ -577,6 +577,78 @@ __device__ __forceinline__ bool group_any(bool b, unsigned mask)
     return (__ballot_sync(mask, b) & mask) != 0u;
 }
 
+// Shared-memory transpose reduction of the projection for groups of a whole warp: per warp, 32
+// rows of 2P partial sums (row stride 2P + 1, odd, so that the column reads are conflict-free)
+// and the 2P totals.
+template <int P, int Q, typename R> struct ProjRed {
+    static constexpr bool value = GroupOf<Q>::G == 32 && sizeof(R) == 4;
+    static constexpr int stride = 2 * P + 1;
+    static constexpr int warp_elems = 32 * stride + 2 * P;
+};
+
+// Projection of the node values onto the basis (the collisional matrices K1 + K2 of Eqs.
+// (28)-(30)): cx_h = sum_q w_q Psi_h(z_q) kx_q, summed over the G lanes of the group (lane r holds
+// nodes r, r + G, ...); every lane receives all 2P coefficients.  FP32 whole-warp groups: each
+// lane writes its 2P partial sums to shared memory (red: this block's ProjRed area, one per warp),
+// lane j adds column j over the 32 lanes in a fixed order, and every lane reads the 2P totals back
+// (~2P shared stores and loads per lane instead of 2P five-level shuffle butterflies).  Otherwise
+// butterfly shuffles.
+template <int P, int Q, typename R>
+__device__ __forceinline__ void project_group(const Nodes<P, Q, R> &nd, const R kx[GroupOf<Q>::NPL],
+                                              const R ky[GroupOf<Q>::NPL], int r, unsigned gmask, R cx[P], R cy[P],
+                                              R *red)
+{
+    constexpr int G = GroupOf<Q>::G, NPL = GroupOf<Q>::NPL;
+    constexpr int S = ProjRed<P, Q, R>::stride;
+    R *w = red + (threadIdx.x >> 5) * ProjRed<P, Q, R>::warp_elems;   // used by ProjRed shapes only
+#pragma unroll (P * Q <= 64 ? P : 1)
+    for (int h = 0; h < P; ++h) {
+        R sx = (R)0, sy = (R)0;
+        if constexpr (sizeof(R) == 4 && !TensorShape<P, Q>::value) {
+            F2 s2 = f2_pack(0.f, 0.f);
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) s2 = f2_fma(f2_pack(kx[s], ky[s]), nd.wpsi2[q * P + h], s2);
+            }
+            f2_unpack(s2, sx, sy);
+        } else {
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) {
+                    sx += nd.wpsi[q * P + h] * kx[s];
+                    sy += nd.wpsi[q * P + h] * ky[s];
+                }
+            }
+        }
+        if constexpr (ProjRed<P, Q, R>::value) {
+            w[r * S + h] = sx;
+            w[r * S + P + h] = sy;
+        } else {
+            cx[h] = group_sum<G>(sx, gmask);
+            cy[h] = group_sum<G>(sy, gmask);
+        }
+    }
+    if constexpr (ProjRed<P, Q, R>::value) {
+        R *tot = w + 32 * S;
+        __syncwarp(gmask);
+        for (int v = r; v < 2 * P; v += 32) {
+            R acc = (R)0;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) acc += w[l * S + v];
+            tot[v] = acc;
+        }
+        __syncwarp(gmask);
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+            cx[h] = tot[h];
+            cy[h] = tot[P + h];
+        }
+        __syncwarp(gmask);   // all lanes have read the totals before the next projection writes
+    }
+}
+
 // Everything the collision loop of one particle needs about its ensemble.
 template <typename R>
 struct P2Target {
@@ -593,6 +665,7 @@ struct P2Target {
     uint32_t *queue_next = nullptr, *qcount_next = nullptr, *mark_next = nullptr;
     double *momN = nullptr;          // [Q*3] moments of step n + 1
     bool out_next = false;
+    R *red = nullptr;                // shared-memory area of project_group (ProjRed shapes)
 };
 
 struct P2Counts { unsigned long long att = 0, chg = 0, rej = 0, cap = 0, oog = 0; };
@@ -668,30 +741,7 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         }
         if (group_any<G>(changed, gmask) && r == 0) ++cnt.chg;
         // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
-#pragma unroll (P * Q <= 64 ? P : 1)
-        for (int h = 0; h < P; ++h) {
-            R sx = (R)0, sy = (R)0;
-            if constexpr (sizeof(R) == 4 && !TensorShape<P, Q>::value) {
-                F2 s2 = f2_pack(0.f, 0.f);
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    const int q = r + s * G;
-                    if (q < Q) s2 = f2_fma(f2_pack(kx[s], ky[s]), nd.wpsi2[q * P + h], s2);
-                }
-                f2_unpack(s2, sx, sy);
-            } else {
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    const int q = r + s * G;
-                    if (q < Q) {
-                        sx += nd.wpsi[q * P + h] * kx[s];
-                        sy += nd.wpsi[q * P + h] * ky[s];
-                    }
-                }
-            }
-            cx[h] = group_sum<G>(sx, gmask);
-            cy[h] = group_sum<G>(sy, gmask);
-        }
+        project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, t.red);
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
@@ -783,7 +833,7 @@ __device__ __forceinline__ void stage(uint32_t *dst, const T &src)
 // Phase 2 of one block, block bid of the nb blocks doing phase 2 (any block size that is a
 // multiple of the group size).
 template <int P, int Q, typename R, bool EXT>
-__device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid, int nb)
+__device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid, int nb, R *red)
 {
     constexpr int G = GroupOf<Q>::G;
     __shared__ double smom[Q * 3];
@@ -812,6 +862,7 @@ __device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid
     P2Target<R> t;
     t.khat = a.khat; t.ld = a.ld; t.Hcur = a.Hcur; t.Hnext = a.Hnext; t.nmax = a.nmax; t.mom = smom;
     t.key0 = a.key0; t.key1 = a.key1; t.stream_id = a.stream_id; t.step = a.step; t.out_step = a.out_step != 0;
+    t.red = red;
     if constexpr (EXT) {
         t.Hnext2 = a.Hnext2; t.queue_next = a.queue_next; t.qcount_next = a.qcount_next; t.mark_next = a.mark_next;
         t.momN = smomN; t.out_next = a.out_next != 0;
@@ -843,7 +894,8 @@ template <int P, int Q, typename R, bool EXT>
 __global__ void __launch_bounds__(kPhase2Threads, 4)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
-    phase2_block<P, Q, R, EXT>(a, blockIdx.x, gridDim.x);
+    __shared__ R sred[ProjRed<P, Q, R>::value ? (kPhase2Threads / 32) * ProjRed<P, Q, R>::warp_elems : 1];
+    phase2_block<P, Q, R, EXT>(a, blockIdx.x, gridDim.x, sred);
 }
 
 // One launch per time step in the pipelined form: blocks [0, nb2) run phase 2 of step n - 1 with
@@ -854,8 +906,8 @@ template <int P, int Q, typename R>
 __global__ void __launch_bounds__(kPhase1Threads, kPhase1MinBlocks<P, Q, R>::value)
 k_step(const __grid_constant__ StepArgs<P, Q, R> a1, const __grid_constant__ StepArgs<P, Q, R> a2, int nb2)
 {
-    extern __shared__ uint32_t swin[];
-    if ((int)blockIdx.x < nb2) phase2_block<P, Q, R, true>(a2, blockIdx.x, nb2);
+    extern __shared__ uint32_t swin[];   // phase 1: histogram window; phase 2: projection area
+    if ((int)blockIdx.x < nb2) phase2_block<P, Q, R, true>(a2, blockIdx.x, nb2, reinterpret_cast<R *>(swin));
     else phase1_block<P, Q, R>(a1, blockIdx.x - nb2, gridDim.x - nb2, swin);
 }
 

@@ -175,10 +175,18 @@ public:
     static constexpr bool kFused = 2 * sizeof(StepArgs<P, Q, R>) + sizeof(int) <= 32764;
     bool fused() const override { return kFused; }
 
+    // dynamic shared memory of the fused kernel: the phase-1 window, or the projection area of
+    // its phase-2 blocks (ProjRed shapes), whichever is larger
+    size_t fused_smem() const
+    {
+        const size_t red = ProjRed<P, Q, R>::value ? (size_t)(kPhase1Threads / 32) * ProjRed<P, Q, R>::warp_elems * sizeof(R) : 0;
+        return std::max(win_bytes_, red);
+    }
+
     bool fused_attr()
     {
         if constexpr (kFused)
-            return cudaFuncSetAttribute(k_step<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_) == cudaSuccess;
+            return cudaFuncSetAttribute(k_step<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem()) == cudaSuccess;
         return true;
     }
 
@@ -195,7 +203,7 @@ public:
         a1.tilectr = b_.qcount + 4 + (int)(n % kQSlots);
         a2.out_step = out_prev ? 1 : 0;
         a2.out_next = out_n ? 1 : 0;
-        k_step<P, Q, R><<<grid2f_ + grid1_, kPhase1Threads, win_bytes_, s>>>(a1, a2, grid2f_);
+        k_step<P, Q, R><<<grid2f_ + grid1_, kPhase1Threads, fused_smem(), s>>>(a1, a2, grid2f_);
         count_launch();
         return cudaGetLastError();
         }

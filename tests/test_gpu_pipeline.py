@@ -87,3 +87,13 @@ def test_pipeline_unavailable_for_36_nodes_fp64():
     s.set_pipeline(False)
     s.step(3, 0)
     s.close()
+
+
+@pytest.mark.parametrize("N", [1, 33, 1023, 1025, 4 * 1024 * 3 + 7])
+def test_pipelined_ragged_sizes(N):
+    """Ensembles smaller than one phase-1 tile, around a tile edge and ragged: same results as the
+    two-launch form, moments on every step."""
+    p = W.scaled(W.GAP_UQ_1E6, N=N, precision="fp64")
+    a = _run(p, [9, 2], 1, pipeline=True)
+    b = _run(p, [9, 2], 1, pipeline=False)
+    _compare(a, b, 1e-12)
