@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             if verbose and out:
                 print(out, file=sys.stderr)
     tmp = LIB + ".tmp%d" % os.getpid()
-    run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
+    run([nvcc] + ARCH + ["-shared", "-cudart", "shared", "-lpthread", "-o", tmp] + objs)
     os.replace(tmp, LIB)
     return LIB
 

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -344,6 +345,24 @@ cudaError_t launch_finalize(const pgc_ctx *ctx, const double *part, int g1, doub
 }  // namespace pgc
 
 using namespace pgc;
+
+// Runs fn(lo, hi) over [0, n) on up to 16 host threads (one for small n): the layout conversions
+// of the state transfers touch every coefficient of the ensemble.
+template <typename F>
+static void host_parallel(int64_t n, F &&fn)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t nt = std::min<int64_t>({(int64_t)std::min(hw, 16u), std::max<int64_t>(1, n / (1 << 18)), n});
+    if (nt <= 1) { fn((int64_t)0, n); return; }
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (int64_t t = 1; t < nt; ++t) {
+        const int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+        if (lo < hi) th.emplace_back([&fn, lo, hi] { fn(lo, hi); });
+    }
+    fn((int64_t)0, std::min(n, chunk));
+    for (auto &x : th) x.join();
+}
 
 static void *staging(pgc_ctx *ctx, size_t bytes)
 {
@@ -774,9 +793,11 @@ pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat)
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
     for (int p = 0; p < 2 * P; ++p)
-        for (int64_t i = 0; i < N; ++i)
-            h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp)[(size_t)p * ld + i]
-                                            : (double)((const float *)tmp)[(size_t)p * ld + i];
+        host_parallel(N, [&](int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i)
+                h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp)[(size_t)p * ld + i]
+                                                : (double)((const float *)tmp)[(size_t)p * ld + i];
+        });
     return PGC_OK;
 }
 
@@ -794,11 +815,13 @@ pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
     char *tmp = (char *)staging(ctx, bytes);
     if (!tmp) return fail(ctx, PGC_ENOMEM, "pinned staging buffer");
     for (int p = 0; p < 2 * P; ++p) {
-        for (int64_t i = 0; i < N; ++i) {
-            const double v = h_khat[(size_t)p * N + i];
-            if (f64) ((double *)tmp)[(size_t)p * ld + i] = v;
-            else ((float *)tmp)[(size_t)p * ld + i] = (float)v;
-        }
+        host_parallel(N, [&](int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) {
+                const double v = h_khat[(size_t)p * N + i];
+                if (f64) ((double *)tmp)[(size_t)p * ld + i] = v;
+                else ((float *)tmp)[(size_t)p * ld + i] = (float)v;
+            }
+        });
         for (int64_t i = N; i < ld; ++i) {
             if (f64) ((double *)tmp)[(size_t)p * ld + i] = 0.0;
             else ((float *)tmp)[(size_t)p * ld + i] = 0.0f;
