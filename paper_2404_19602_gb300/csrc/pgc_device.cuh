@@ -326,21 +326,23 @@ __device__ __forceinline__ bool pauli_accept(uint32_t H, uint32_t nmax, uint32_t
 template <typename T>
 __host__ __device__ inline T li2_bern(T x)
 {
-    // x in [-1, 0]:  Li2(x) = sum_n B_n t^{n+1}/(n+1)!,  t = -ln(1 - x),  |t| <= ln 2
+    // x in [-1, 0]:  Li2(x) = sum_n B_n t^{n+1}/(n+1)!,  t = -ln(1 - x),  |t| <= ln 2;
+    // B_0 t + B_1 t^2/2 + t^3 sum_k c_k (t^2)^k with c_k = B_{2k+2} / (2k+3)!, by Horner (no
+    // divisions: on this GPU FP64 division is the dominant cost of the Fermi-Dirac inversion)
     const T t = -log1p(-x);
-    const T B[12] = {(T)(1.0 / 6.0), (T)(-1.0 / 30.0), (T)(1.0 / 42.0), (T)(-1.0 / 30.0), (T)(5.0 / 66.0),
-                     (T)(-691.0 / 2730.0), (T)(7.0 / 6.0), (T)(-3617.0 / 510.0), (T)(43867.0 / 798.0),
-                     (T)(-174611.0 / 330.0), (T)(854513.0 / 138.0), (T)(-236364091.0 / 2730.0)};
-    T s = t - (T)0.25 * t * t;  // B_0 t + B_1 t^2 / 2
-    T t2 = t * t, p = t * t2, fact = (T)6;  // t^3 / 3!
-    const int nterms = (sizeof(T) == 8) ? 12 : 5;
-    for (int k = 0; k < nterms; ++k) {
-        s += B[k] * p / fact;
-        const T n = (T)(2 * k + 3);  // next odd power
-        p *= t2;
-        fact *= (n + (T)1) * (n + (T)2);
-    }
-    return s;
+    constexpr double c[12] = {(1.0 / 6.0) / 6.0, (-1.0 / 30.0) / 120.0, (1.0 / 42.0) / 5040.0,
+                              (-1.0 / 30.0) / 362880.0, (5.0 / 66.0) / 39916800.0,
+                              (-691.0 / 2730.0) / 6227020800.0, (7.0 / 6.0) / 1307674368000.0,
+                              (-3617.0 / 510.0) / 355687428096000.0, (43867.0 / 798.0) / 121645100408832000.0,
+                              (-174611.0 / 330.0) / 51090942171709440000.0,
+                              (854513.0 / 138.0) / 25852016738884976640000.0,
+                              (-236364091.0 / 2730.0) / 15511210043330985984000000.0};
+    constexpr int nterms = (sizeof(T) == 8) ? 12 : 5;
+    const T t2 = t * t;
+    T poly = (T)c[nterms - 1];
+#pragma unroll
+    for (int k = nterms - 2; k >= 0; --k) poly = poly * t2 + (T)c[k];
+    return t - (T)0.25 * t2 + t * t2 * poly;
 }
 
 template <typename T>
@@ -368,9 +370,9 @@ __host__ __device__ inline T fd_upper(T e, T mu, T kT)
 // checked in FP64, then safeguarded Newton in FP64 (plain FP64 bisection if the check fails).
 __host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, double u)
 {
-    const double tot = fd_upper<double>(eps0, mu, kT);
+    const double tot = fd_upper<double>(eps0, mu, kT), itot = 1.0 / tot;
     auto resid = [&](double e) {  // F(e) - u  (upper-tail form for u >= 1/2)
-        return (u < 0.5) ? (tot - fd_upper<double>(e, mu, kT)) / tot - u : (1.0 - u) - fd_upper<double>(e, mu, kT) / tot;
+        return (u < 0.5) ? (tot - fd_upper<double>(e, mu, kT)) * itot - u : (1.0 - u) - fd_upper<double>(e, mu, kT) * itot;
     };
     const double top = fmax(mu, eps0) + 80.0 * kT;
     double lo = eps0, hi = top;
@@ -402,7 +404,7 @@ __host__ __device__ inline double fd_inverse(double eps0, double mu, double kT, 
         const double r = resid(e);
         if (r == 0.0) break;  // exact root
         if (r < 0.0) lo = e; else hi = e;
-        const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) / tot;
+        const double dens = e / (1.0 + exp(fmin((e - mu) / kT, 700.0))) * itot;
         double en = (dens > 0.0) ? e - r / dens : 0.5 * (lo + hi);
         if (!(en >= lo && en <= hi)) en = 0.5 * (lo + hi);  // keep the iterate in the bracket
         const double step = fabs(en - e);
