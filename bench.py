@@ -175,9 +175,22 @@ def cpu_baseline(p):
     t0 = time.perf_counter()
     o.step(steps, p.get("moments_every", 10))
     dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+    cores = O.num_threads()
+    # the same oracle on one core, on a tenth of the sample
+    n1, s1 = max(n // 10, 200), max(steps // 3, 10)
+    O.set_threads(1)
+    try:
+        o1 = O.Oracle(W.scaled(p, N=n1))
+        t1 = time.perf_counter()
+        o1.step(s1, p.get("moments_every", 10))
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(0)
+    return {"value": n * steps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": "%d particles x %d time steps of the same workload (FP64, OpenMP)" % (n, steps),
-            "seconds": round(dt, 3)}
+            "seconds": round(dt, 3),
+            "single_core": {"value": n1 * s1 / dt1, "sample": "%d particles x %d time steps, 1 thread" % (n1, s1),
+                            "seconds": round(dt1, 3)}}
 
 
 def run_reference(args):

@@ -115,6 +115,7 @@ def lib():
             L.orc_set_step.argtypes = [vp, C.c_int64]
             L.orc_set_nmax.argtypes = [vp, u32p]
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
 
@@ -199,6 +200,11 @@ def angle_k(u):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_threads(n: int):
+    """Threads of the oracle's parallel loops (n <= 0: all host cores)."""
+    lib().orc_set_threads(int(n))
 
 
 class Oracle:

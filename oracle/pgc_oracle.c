@@ -1080,6 +1080,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* threads of the following parallel loops (n <= 0: all host cores); for timing the oracle */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Pathwise sensitivities by forward-mode tangents (test reference for the adjoint).          */
 /*                                                                                            */
