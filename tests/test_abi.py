@@ -94,3 +94,26 @@ def test_oracle_and_library_share_no_code():
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2404_19602_gb300" not in txt, f
             assert "pgc.h" not in txt and "csrc" not in txt, f
+
+
+def test_band_minimum_law_fields_are_checked(lib):
+    """The width law needs a positive, ordered width interval; an unknown law is rejected."""
+    cfg = pgc.pgc_config_default()
+    cfg.eps0_law = 7
+    with pytest.raises(pgc.PgcError) as e:
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EINVAL
+    cfg = pgc.pgc_config_default()
+    cfg.eps0_law = pgc.PGC_EPS0_WIDTH
+    cfg.width_nm.lo, cfg.width_nm.hi = 0.0, 0.0
+    with pytest.raises(pgc.PgcError):
+        pgc.pgc_query_sizes(cfg)
+    cfg.width_nm.lo, cfg.width_nm.hi = 7.5, 6.5
+    with pytest.raises(pgc.PgcError):
+        pgc.pgc_query_sizes(cfg)
+    cfg.width_nm.lo, cfg.width_nm.hi = 6.5, 7.5
+    s = pgc.pgc_query_sizes(cfg)
+    assert (s["P"], s["Q"]) == (6, 6)
+    cfg.width_nm.hi = 6.5                      # a deterministic width: no random input
+    s = pgc.pgc_query_sizes(cfg)
+    assert (s["P"], s["Q"]) == (1, 1)
