@@ -341,11 +341,15 @@ class Simulation:
         self.d = int(self.cfg.eps0_eV.lo != self.cfg.eps0_eV.hi) + int(self.cfg.Ex_Vcm.lo != self.cfg.Ex_Vcm.hi)
         self.max_outputs = max_outputs
         dev = torch.device("cuda", torch.cuda.current_device())
-        # torch's caching allocator returns 512-byte aligned blocks
-        self.state_buf = torch.empty(sz["state_bytes"], dtype=torch.uint8, device=dev)
-        self.hist_buf = torch.empty(sz["hist_bytes"], dtype=torch.uint8, device=dev)
-        self.scratch_buf = torch.empty(sz["scratch_bytes"], dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # Allocated with the context's stream current: torch's caching allocator then orders any
+        # reuse of these blocks after the work queued on that stream (allocated under another
+        # stream, a block freed there could be handed to this context while earlier work on it is
+        # still pending).  The allocator returns 512-byte aligned blocks.
+        with torch.cuda.stream(self.stream):
+            self.state_buf = torch.empty(sz["state_bytes"], dtype=torch.uint8, device=dev)
+            self.hist_buf = torch.empty(sz["hist_bytes"], dtype=torch.uint8, device=dev)
+            self.scratch_buf = torch.empty(sz["scratch_bytes"], dtype=torch.uint8, device=dev)
         self.ctx = pgc_init(self.cfg, self.state_buf.data_ptr(), self.hist_buf.data_ptr(),
                             self.scratch_buf.data_ptr(), init_khat, self.stream.cuda_stream)
 
@@ -396,7 +400,8 @@ class BatchSimulation:
         self.sims = [Simulation(p, max_outputs=max_outputs, stream=self.stream) for p in cases]
         ctxs = [s.ctx for s in self.sims]
         n = pgc_batch_query_sizes(ctxs)
-        self.scratch_buf = torch.empty(max(n, 256), dtype=torch.uint8, device=self.sims[0].state_buf.device)
+        with torch.cuda.stream(self.stream):   # allocated on the stream the batch runs on
+            self.scratch_buf = torch.empty(max(n, 256), dtype=torch.uint8, device=self.sims[0].state_buf.device)
         self.batch = pgc_batch_create(ctxs, self.scratch_buf.data_ptr(), tile)
 
     def step(self, n_steps: int, moments_every: int = 0, use_graph: bool = True):
@@ -437,7 +442,8 @@ def adjoint(params: dict, n_steps: int, ckpt_every: int, moments_every: int, win
 
     sim = Simulation(params, max_outputs=n_steps // moments_every + 2)
     nbytes = pgc_adjoint_query_sizes(sim.ctx, n_steps, ckpt_every)
-    work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=sim.state_buf.device)
+    with torch.cuda.stream(sim.stream):
+        work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=sim.state_buf.device)
     val, grad = pgc_adjoint(sim.ctx, n_steps, ckpt_every, moments_every, window_steps, weights, work.data_ptr())
     sim.close()
     return val, grad

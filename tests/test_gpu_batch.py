@@ -103,3 +103,24 @@ def test_batch_rejects_mismatched_cases():
     c = pgc.Simulation(W.scaled(W.GAP_UQ_1E6, N=100, precision="fp64"))
     with pytest.raises(pgc.PgcError):
         pgc.pgc_batch_query_sizes([a.ctx, c.ctx])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_then_pipelined_single_steps(prec):
+    """Contexts advanced by the batch and then alone (pipelined form, which keeps its own collider
+    bitmaps and queue counters) follow the standalone trajectory."""
+    from paper_2404_19602_gb300 import pgc
+
+    cases = _cases(prec, ns=(3000, 1700))
+    b = pgc.BatchSimulation(cases, max_outputs=8, tile=1024)
+    b.step(10, 5, use_graph=True)
+    torch.cuda.synchronize()
+    for p, sim in zip(cases, b.sims):
+        sim.set_pipeline(True)
+        sim.step(12, 0)
+        ks, _, hs, cs = _single(p, 22, 5)
+        assert np.array_equal(sim.state(), ks), p["stream_id"]
+        assert np.array_equal(sim.hist()[0], hs)
+        for k in ("attempts", "changed", "rejected", "steps"):
+            assert sim.counters()[k] == cs[k], k
+    b.close()
