@@ -49,6 +49,9 @@
  *             series, counters, a device copy of the node tables).
  * All calls on a context are ordered on the CUDA stream given to pgc_init; calls that return
  * host data (pgc_moments, pgc_get_state, pgc_counters, pgc_reconstruct_f) synchronize it.
+ * The buffers are read and written by work queued on that stream: a caller that frees or reuses
+ * them must do so behind that work (with a stream-ordered allocator, allocate them on that
+ * stream); pgc_init's own initialisation of the buffers is queued on that stream too.
  *
  * Errors
  * ------
