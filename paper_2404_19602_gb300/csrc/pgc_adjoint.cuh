@@ -80,6 +80,17 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
     const Phys<R> &ph = a.ph;
     const Nodes<P, Q, R> &nd = a.nd;
     double g[NTH] = {0.0, 0.0, 0.0, 0.0};
+    // The drift and moment terms of the gradient are linear in per-particle quantities: for the
+    // small shapes each thread sums those over its particles (in R) and applies the FP64
+    // coefficients once at the end, instead of FP64 multiply-adds per particle (FP64 throughput
+    // is low on this GPU).
+    constexpr bool kSums = P * Q <= 64;
+    constexpr int SP = kSums ? P : 1, SQ = kSums ? Q : 1;
+    R slx[SP], svh[SQ], sdve[SQ];
+#pragma unroll
+    for (int h = 0; h < SP; ++h) slx[h] = (R)0;
+#pragma unroll
+    for (int q = 0; q < SQ; ++q) { svh[q] = (R)0; sdve[q] = (R)0; }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.N; base += stride) {
@@ -118,9 +129,14 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
                         lx[h] += gx * nd.psi[q * P + h];
                         ly[h] += gy * nd.psi[q * P + h];
                     }
+                    if constexpr (kSums) {
+                        svh[q] += vhat;
+                        sdve[q] += dve;
+                    } else {
 #pragma unroll
-                    for (int t = 0; t < NTH; ++t)
-                        g[t] += s * (a.dnq[q] * a.de0[q][t] * (double)vhat + a.nq[q] * (double)dve * a.de0[q][t]);
+                        for (int t = 0; t < NTH; ++t)
+                            g[t] += s * (a.dnq[q] * a.de0[q][t] * (double)vhat + a.nq[q] * (double)dve * a.de0[q][t]);
+                    }
                 }
 #pragma unroll
                 for (int h = 0; h < P; ++h) {
@@ -144,12 +160,17 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
             const R gub = ph.alpha1 * rate_bound(ph, emax, nd.eps0_max) * (R)1.0001;
             maybe = lnxi < gub * ph.dt;
             if (!maybe) {  // lambda* = lambda: drift term -sum_h d dhat_h/d theta lambda_x,h
+                if constexpr (kSums) {
 #pragma unroll
-                for (int t = 0; t < NTH; ++t) {
-                    double s = 0.0;
+                    for (int h = 0; h < P; ++h) slx[h] += lx[h];
+                } else {
 #pragma unroll
-                    for (int h = 0; h < P; ++h) s += a.ddhat[t][h] * (double)lx[h];
-                    g[t] -= s;
+                    for (int t = 0; t < NTH; ++t) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int h = 0; h < P; ++h) s += a.ddhat[t][h] * (double)lx[h];
+                        g[t] -= s;
+                    }
                 }
             }
         }
@@ -161,6 +182,23 @@ k_adj_screen(const __grid_constant__ AdjArgs<P, Q, R> a)
             basepos = __shfl_sync(0xffffffffu, basepos, leader);
             if (maybe) a.queue[basepos + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)i;
         }
+    }
+    if constexpr (kSums) {
+#pragma unroll
+        for (int t = 0; t < NTH; ++t) {
+            double s = 0.0;
+#pragma unroll
+            for (int h = 0; h < P; ++h) s += a.ddhat[t][h] * (double)slx[h];
+            g[t] -= s;
+        }
+        if (a.inject)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const double s = a.dLdJ[q] * a.cJ;
+#pragma unroll
+                for (int t = 0; t < NTH; ++t)
+                    g[t] += s * (a.dnq[q] * a.de0[q][t] * (double)svh[q] + a.nq[q] * (double)sdve[q] * a.de0[q][t]);
+            }
     }
     block_add_grad<P, Q, R>(a.grad, g);
 }
