@@ -183,6 +183,20 @@ pgc_status pgc_moments(pgc_ctx *ctx, double *h_t_fs, double *h_mean, double *h_v
 pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32_t *h_hist,
                              uint32_t *h_max);
 
+/* Observables of the current state at nz arbitrary points h_z[nz][d] in [-1,1]^d (d = number of
+ * random inputs; h_z may be NULL when d = 0): every particle is reconstructed at z by Eq. (23),
+ * and h_out[nz][4] receives the ensemble averages of Eqs. (35)-(37) at that z: V_x, V_y (m/s), the
+ * mean energy (eV) and J_x = -e n(z) V_x (A/m, n of Eq. (31) at the band minimum eps0(z)).
+ * At a quadrature node this is the node value pgc_moments reports.  Evaluated at many z drawn
+ * from the input distribution, the values give the distribution of an observable over z, e.g.
+ * the central 80 % band of Test 2 (Sec. 5) as its 10 % and 90 % quantiles.
+ * Arithmetic: reconstruction, velocity and energy in the state precision, sums over groups of
+ * particles in that precision, then FP64 in a fixed order (results are reproducible run to run).
+ * Cost: one pass over the state per 32 points.  Synchronizes the context stream.
+ * Errors: PGC_EINVAL for nz < 0, a NULL h_out (nz > 0), a NULL h_z (nz > 0, d > 0) or a
+ * coordinate outside [-1,1]. */
+pgc_status pgc_observe_at(pgc_ctx *ctx, const double *h_z, int32_t nz, double *h_out);
+
 /* State as FP64 on the host, layout [2][P][N] (synchronizes), and the reverse upload (the
  * histogram of the uploaded state becomes f^n for the next step). */
 pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat);

@@ -304,6 +304,36 @@ k_finalize(const double *part1, const double *part2, const double *part3, const 
     }
 }
 
+// Observables at arbitrary points from the block partials of k_obs_at (fixed order over the
+// blocks): out[z] = (V_x, V_y, energy, J_x) as in the records of k_finalize.
+struct ObsFin {
+    double n[kObsZ];   // density n(eps0(z)) (m^-2)
+    double scale_v;    // hbar vF * vF / N: sum of kx/eps -> V_x in m/s
+    double inv_N;
+    int nz, g;
+};
+
+__global__ void __launch_bounds__(128)
+k_obs_fin(const double *part, const __grid_constant__ ObsFin f, double *out)
+{
+    __shared__ double S[kObsZ * 3];
+    const int t = threadIdx.x;
+    if (t < kObsZ * 3) {
+        double s = 0.0;
+        for (int b = 0; b < f.g; ++b) s += part[(int64_t)b * kObsZ * 3 + t];
+        S[t] = s;
+    }
+    __syncthreads();
+    if (t < f.nz) {
+        const double qe = 1.602176634e-19;
+        const double vx = S[t * 3 + 0] * f.scale_v, vy = S[t * 3 + 1] * f.scale_v;
+        out[t * 4 + 0] = vx;
+        out[t * 4 + 1] = vy;
+        out[t * 4 + 2] = S[t * 3 + 2] * f.inv_N;
+        out[t * 4 + 3] = -qe * f.n[t] * vx;
+    }
+}
+
 // maximum over the cells of each node's histogram
 __global__ void k_hist_max(const uint32_t *H, int64_t cells, uint32_t *out)
 {
@@ -426,7 +456,8 @@ struct Layout {
     int64_t ld = 0, hist_stride = 0, queue_stride = 0, mark_words = 0;
     size_t state = 0, hist = 0, scratch = 0;
     size_t off_queue = 0, off_qcount = 0, off_counters = 0, off_nmax = 0, off_part1 = 0, off_part2 = 0,
-           off_partN = 0, off_marks = 0, off_tables = 0, off_series = 0, off_recon = 0, off_tmpmax = 0;
+           off_partN = 0, off_marks = 0, off_tables = 0, off_series = 0, off_recon = 0, off_tmpmax = 0,
+           off_obs = 0;
     int rec_len = 0;
 };
 }  // namespace
@@ -487,6 +518,7 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     L->off_series = take((size_t)c->max_outputs * L->rec_len * 8);
     L->off_recon = take((size_t)c->Nk * c->Nk * 4);
     L->off_tmpmax = take(4);
+    L->off_obs = take((size_t)(kObsGrid * kObsZ * 3 + kObsZ * 4) * 8);
     L->scratch = off;
     return PGC_OK;
 }
@@ -616,6 +648,8 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     b.stream_id = cfg->stream_id;
     ctx->series = (double *)(scr + L.off_series);
     ctx->tmp_max = (uint32_t *)(scr + L.off_tmpmax);
+    ctx->obs_part = (double *)(scr + L.off_obs);
+    ctx->obs_out = ctx->obs_part + (size_t)kObsGrid * kObsZ * 3;
     ctx->rec_len = L.rec_len;
     ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
     // the fused step overlaps the collider work with the streaming work.  For 36 nodes the
@@ -892,6 +926,47 @@ pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "reconstruct_f");
     }
+    return PGC_OK;
+}
+
+pgc_status pgc_observe_at(pgc_ctx *ctx, const double *h_z, int32_t nz, double *h_out)
+{
+    if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const int d = ctx->t.d, P = ctx->t.P;
+    if (nz < 0 || (nz > 0 && (!h_out || (!h_z && d > 0)))) return fail(ctx, PGC_EINVAL, "bad arguments");
+    for (int64_t j = 0; j < (int64_t)nz * d; ++j)
+        if (!(h_z[j] >= -1.0 && h_z[j] <= 1.0)) return fail(ctx, PGC_EINVAL, "z outside [-1,1]");
+    const HostTables &t = ctx->t;
+    std::vector<double> psi((size_t)kObsZ * P), e0(kObsZ);
+    for (int j0 = 0; j0 < nz; j0 += kObsZ) {
+        const int nzc = std::min(kObsZ, nz - j0);
+        ObsFin f{};
+        for (int l = 0; l < nzc; ++l) {
+            const double *z = d ? &h_z[(size_t)(j0 + l) * d] : nullptr;
+            basis_at(d, ctx->cfg.degree_M, z, &psi[(size_t)l * P]);
+            // z1 is the band-minimum variable when the band minimum is random
+            const double ze = ((d == 1 && t.eps_random) || d == 2) ? z[0] : 0.0;
+            e0[l] = eps0_at(ctx->cfg, t.hvF, ze);
+            f.n[l] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper<double>(e0[l], ctx->cfg.eps_F_eV, t.kT) * 1.0e18;
+        }
+        int g = 0;
+        cudaError_t e = ctx->run->obs_at(psi.data(), e0.data(), nzc, ctx->obs_part, &g, ctx->stream);
+        if (e == cudaSuccess) {
+            f.scale_v = t.hvF * t.vF_ms / (double)ctx->b.N;
+            f.inv_N = 1.0 / (double)ctx->b.N;
+            f.nz = nzc;
+            f.g = g;
+            k_obs_fin<<<1, 128, 0, ctx->stream>>>(ctx->obs_part, f, ctx->obs_out);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out + (size_t)j0 * 4, ctx->obs_out, (size_t)nzc * 4 * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "observe_at");
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "observe_at");
     return PGC_OK;
 }
 

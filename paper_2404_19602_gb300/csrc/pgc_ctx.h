@@ -20,6 +20,8 @@ struct pgc_ctx {
     int rec_len = 0;
     double *series = nullptr;
     uint32_t *tmp_max = nullptr;
+    double *obs_part = nullptr;  // [kObsGrid][kObsZ][3] block partials of pgc_observe_at
+    double *obs_out = nullptr;   // [kObsZ][4]
     bool failed = false;
     bool sampled = false;  // state comes from the initial Fermi-Dirac sampling (no upload since)
     std::string err;

@@ -1026,4 +1026,108 @@ k_hist_at(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ R
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Observables at arbitrary points z (Eqs. (35)-(37) of the state reconstructed by Eq. (23) off
+// the nodes).  Lane l of every warp evaluates point z_l; a block stages a tile of particles in
+// shared memory as (x, y) coefficient pairs and each warp walks a share of the tile, every lane
+// reading the same particle (broadcast).  Sums: in R over the particles of one tile, then FP64;
+// block partials [kObsGrid][kObsZ][3] = (sum kx/eps, sum ky/eps, sum eps), reduced over the
+// blocks in a fixed order by k_obs_fin.
+// ------------------------------------------------------------------------------------------
+constexpr int kObsZ = 32;        // points per pass over the state (one per lane)
+constexpr int kObsGrid = 304;    // blocks of one pass (2 per SM)
+constexpr int kObsThreads = 256;
+
+template <int P, typename R>
+struct ObsTile {   // particles per tile: the staged pairs take at most 32 KB
+    static constexpr int value = (2 * P * (int)sizeof(R) * 256 <= 32768) ? 256
+                               : (2 * P * (int)sizeof(R) * 128 <= 32768) ? 128 : 64;
+};
+
+template <int P, typename R>
+struct ObsArgs {
+    const R *khat;
+    int64_t ld, N;
+    R hvF2;
+    R psi[kObsZ * P];   // basis at each point; zero rows for unused lanes
+    R e0sq[kObsZ];      // eps0(z)^2; 1 for unused lanes
+};
+
+template <typename R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+
+template <int P, typename R>
+__global__ void __launch_bounds__(kObsThreads)
+k_obs_at(const __grid_constant__ ObsArgs<P, R> a, double *part)
+{
+    constexpr int T = ObsTile<P, R>::value;
+    constexpr int kWarps = kObsThreads / 32;
+    using R2 = typename Pair<R>::T;
+    __shared__ R2 tile[P * T];
+    __shared__ double red[kWarps][kObsZ * 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    R ps[P];
+#pragma unroll
+    for (int h = 0; h < P; ++h) ps[h] = a.psi[lane * P + h];
+    const R e0sq = a.e0sq[lane];
+    double ax = 0.0, ay = 0.0, ae = 0.0;
+    const int64_t ntiles = (a.N + T - 1) / T;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t base = t * T;
+        const int nv = (a.N - base < (int64_t)T) ? (int)(a.N - base) : T;
+        __syncthreads();   // the previous tile is consumed
+        for (int idx = threadIdx.x; idx < P * T; idx += kObsThreads) {
+            const int h = idx / T, j = idx - h * T;
+            R2 v;
+            v.x = (j < nv) ? a.khat[(int64_t)h * a.ld + base + j] : (R)0;
+            v.y = (j < nv) ? a.khat[(int64_t)(P + h) * a.ld + base + j] : (R)0;
+            tile[h * T + j] = v;
+        }
+        __syncthreads();
+        R sx = (R)0, sy = (R)0, se = (R)0;
+        for (int j = warp; j < nv; j += kWarps) {   // uniform over the warp
+            R kx, ky;
+            if constexpr (sizeof(R) == 4) {
+                F2 s = f2_pack(0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < P; ++h) {
+                    const float2 c = tile[h * T + j];
+                    F2 w;
+                    asm("mov.b64 %0, {%1, %1};" : "=l"(w.v) : "f"(ps[h]));
+                    s = f2_fma(f2_pack(c.x, c.y), w.v, s);
+                }
+                f2_unpack(s, kx, ky);
+            } else {
+                kx = (R)0;
+                ky = (R)0;
+#pragma unroll
+                for (int h = 0; h < P; ++h) {
+                    const R2 c = tile[h * T + j];
+                    kx += c.x * ps[h];
+                    ky += c.y * ps[h];
+                }
+            }
+            const R eps = rsqrt_<R>(a.hvF2 * (kx * kx + ky * ky) + e0sq);
+            const R ie = (R)1 / eps;
+            sx += kx * ie;
+            sy += ky * ie;
+            se += eps;
+        }
+        ax += (double)sx;
+        ay += (double)sy;
+        ae += (double)se;
+    }
+    red[warp][lane * 3 + 0] = ax;
+    red[warp][lane * 3 + 1] = ay;
+    red[warp][lane * 3 + 2] = ae;
+    __syncthreads();
+    if (threadIdx.x < kObsZ * 3) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * kObsZ * 3 + threadIdx.x] = s;
+    }
+}
+
 }  // namespace pgc

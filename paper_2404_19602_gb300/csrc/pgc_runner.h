@@ -81,6 +81,10 @@ public:
     virtual cudaError_t upload_tables(cudaStream_t s) = 0;
     // histogram at one arbitrary z (psi of length P, FP64) into out [Nk*Nk]
     virtual cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) = 0;
+    // block partials of the observables at nzc <= 32 arbitrary points (psi [nzc][P] and the band
+    // minima eps0 [nzc], FP64) into part [blocks][32][3]; *blocks receives the block count
+    virtual cudaError_t obs_at(const double *psi, const double *eps0, int nzc, double *part, int *blocks,
+                               cudaStream_t s) = 0;
 };
 
 // Factories, one per compiled (P, Q) shape; precision 0 = FP32, 1 = FP64.  nullptr if the

@@ -235,6 +235,27 @@ public:
         return cudaGetLastError();
     }
 
+    cudaError_t obs_at(const double *psi, const double *eps0, int nzc, double *part, int *blocks,
+                       cudaStream_t s) override
+    {
+        ObsArgs<P, R> o;
+        o.khat = args_.khat;
+        o.ld = b_.ld;
+        o.N = b_.N;
+        o.hvF2 = args_.ph.hvF2;
+        for (int l = 0; l < kObsZ; ++l) {
+            for (int h = 0; h < P; ++h) o.psi[l * P + h] = (l < nzc) ? (R)psi[(size_t)l * P + h] : (R)0;
+            const R e = (l < nzc) ? (R)eps0[l] : (R)1;
+            o.e0sq[l] = e * e;   // as the node observables square the band minimum
+        }
+        constexpr int T = ObsTile<P, R>::value;
+        const int g = (int)std::min<int64_t>((b_.N + T - 1) / T, kObsGrid);
+        *blocks = g;
+        k_obs_at<P, R><<<g, kObsThreads, 0, s>>>(o, part);
+        count_launch();
+        return cudaGetLastError();
+    }
+
 private:
     void fill_phys(const HostTables &t)
     {

@@ -69,6 +69,7 @@ SIGNATURES = {
     "pgc_set_pipeline": (C.c_int, [_vp, C.c_int32]),
     "pgc_moments": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _i64p]),
     "pgc_reconstruct_f": (C.c_int, [_vp, _dp, C.c_int32, _u32p, _u32p]),
+    "pgc_observe_at": (C.c_int, [_vp, _dp, C.c_int32, _dp]),
     "pgc_get_state": (C.c_int, [_vp, _dp]),
     "pgc_set_state": (C.c_int, [_vp, _dp]),
     "pgc_counters": (C.c_int, [_vp, _u64p]),
@@ -167,6 +168,14 @@ def pgc_reconstruct_f(ctx, z, d: int, Nk: int):
     m = np.zeros(nz, dtype=np.uint32)
     _check(lib().pgc_reconstruct_f(_vp(ctx), _ptr(z, _dp), nz, _ptr(H, _u32p), _ptr(m, _u32p)), _vp(ctx))
     return H, m
+
+
+def pgc_observe_at(ctx, z, d: int):
+    """Observables [nz][4] = (V_x, V_y, energy, J_x) of the current state at the points z."""
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.float64).reshape(-1, max(d, 1)))
+    out = np.zeros((z.shape[0], 4))
+    _check(lib().pgc_observe_at(_vp(ctx), _ptr(z, _dp), z.shape[0], _ptr(out, _dp)), _vp(ctx))
+    return out
 
 
 def pgc_get_state(ctx, P: int, N: int):
@@ -387,6 +396,10 @@ class Simulation:
 
     def reconstruct_f(self, z):
         return pgc_reconstruct_f(self.ctx, z, self.d, self.Nk)
+
+    def observe_at(self, z):
+        """(V_x, V_y, energy, J_x) at each point z (rows of shape [d], in [-1, 1]^d)."""
+        return pgc_observe_at(self.ctx, z, self.d)
 
 
 class BatchSimulation:
