@@ -34,7 +34,8 @@ from paper_2404_19602_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None,
              "adjoint": W.ADJOINT_1E6,
-             "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64")}
+             "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64"),
+             "sg_error": W.TEST3_WIDTH_1E4}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -51,7 +52,8 @@ def parse():
                     help="gap_uq (1e6 particles, 1 random input), det (1e4, FP64), gap_field (4e6, 2 random "
                          "inputs), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
                          "reverse sweep of the steady-current sensitivities, 1e6 particles), gap_uq_fp64 "
-                         "(the gap_uq ensemble in the FP64 mode)")
+                         "(the gap_uq ensemble in the FP64 mode), sg_error (the stochastic-Galerkin error "
+                         "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles)")
     ap.add_argument("--fd-check", action="store_true",
                     help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
@@ -346,6 +348,62 @@ def run_adjoint(args, pgc, torch, dev, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_sg_error(args, pgc, torch, dev, rank, world):
+    """Test 3 (Sec. 5): one step = the stochastic-Galerkin error study of both scenarios
+    (uncertain width, uncertain field): degrees 0..25 and the reference 30 on M + 1 nodes, 1e4
+    particles, dt 2.5 fs, errors of the energy in L2(I_z) at 0.1, 0.5 and 1 ps.  The metric
+    counts the particle-steps of all runs over the device time of their pgc_step calls."""
+    from paper_2404_19602_gb300 import sg_error as SG
+
+    degrees = [M for M in SG.DEGREES if M != 30]
+    scen = {"width": W.TEST3_WIDTH_1E4, "field": W.TEST3_FIELD_1E4}
+    steps = W.TEST3_TIMES_STEPS
+
+    def one():
+        rec = []
+        t0 = time.perf_counter()
+        errs = {k: SG.sg_error(rank_workload(p, rank), degrees, 30, steps, record=rec) for k, p in scen.items()}
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return sum(a.elapsed_time(b) for a, b, _ in rec), sum(n for _, _, n in rec), wall, errs
+
+    for _ in range(args.warmup):
+        one()
+    launches0 = pgc.pgc_launch_count()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    res = [one() for _ in range(args.steps)]
+    clk = clocks.stop()
+    launches = pgc.pgc_launch_count() - launches0
+    ms = max_over_ranks(sum(r[0] for r in res), dev)
+    wall = max_over_ranks(sum(r[2] for r in res), dev)
+    ps = res[0][1]
+    errs = res[-1][3]
+    if rank == 0:
+        dt = W.TEST3_WIDTH_1E4["dt_fs"]
+        line = {
+            "metric": METRIC, "value": ps * world * args.steps / (ms / 1e3), "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "test3_sg_error_width+field_M0-25_ref30_N1e4_dt2.5fs_fp32",
+                       "particles_per_run": W.TEST3_WIDTH_1E4["N"], "runs_per_step": 2 * (len(degrees) + 1),
+                       "particle_steps_per_step": ps, "degrees": degrees, "M_ref": 30,
+                       "l2": "not flushed: each run's 1e4-particle state (<= 2.5 MB) is L2-resident, as in any run of "
+                             "that size"},
+            "roofline": None,
+            "roofline_note": "1e4 particles per run: launch- and latency-bound, as the 1e4-particle deterministic "
+                             "workload; the HBM fraction is not meaningful",
+            "e2e": {"value": ps * world * args.steps / wall, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 2 * (len(degrees) + 1) * len(steps) * 64 * 4 * 8,
+                    "note": "wall clock of the whole study through the public API: context creation, the initial "
+                            "sampling on the device (no state upload), the steps and the observations at 64 points"},
+            "sg_error": {k: {"t_ps": [n * dt / 1000.0 for n in steps], "M": degrees,
+                             "err_eV": [[float(x) for x in v[M]] for M in degrees]} for k, v in errs.items()},
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -369,8 +427,9 @@ def main():
     from paper_2404_19602_gb300 import build as B
 
     B.build()
-    if args.workload in ("sweep", "adjoint"):
-        (run_sweep if args.workload == "sweep" else run_adjoint)(args, pgc, torch, dev, rank, world)
+    if args.workload in ("sweep", "adjoint", "sg_error"):
+        {"sweep": run_sweep, "adjoint": run_adjoint, "sg_error": run_sg_error}[args.workload](
+            args, pgc, torch, dev, rank, world)
         if world > 1:
             dist.destroy_process_group()
         return

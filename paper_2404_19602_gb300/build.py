@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -29,8 +30,18 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpgc.so")
 
 
+ONE_D = "pgc_inst_1d.cu"   # compiled once per one-dimensional shape
+
+
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu") and f != ONE_D)
+
+
+def shapes_1d():
+    """Basis sizes P of the one-dimensional shapes (the PGC_SHAPES_1D list of pgc_runner.h)."""
+    src = open(os.path.join(CSRC, "pgc_runner.h")).read()
+    m = re.search(r"#define PGC_SHAPES_1D\(X\)(.*)", src)
+    return [int(v) for v in re.findall(r"X\((\d+)\)", m.group(1))]
 
 
 def _deps():
@@ -53,10 +64,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     flags = FLAGS + list(extra_flags or [])
     objs = []
     cmds = []
+    for P in sorted(shapes_1d(), reverse=True):   # the largest units first
+        obj = os.path.join(BUILD, "pgc_inst_1d_%d.o" % P)
+        objs.append(obj)
+        cmds.append([nvcc] + ARCH + flags + ["-DPGC_1D_P=%d" % P, "-c", os.path.join(CSRC, ONE_D), "-o", obj])
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc] + ARCH + flags + ["-c", src, "-o", obj])
+    cmds.sort(key=lambda c: "21x36" not in c[-3])   # the longest unit first (stable otherwise)
 
     def run(cmd):
         if verbose:
@@ -66,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         return r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(cmds))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, len(cmds)))) as ex:
         for out in ex.map(run, cmds):
             if verbose and out:
                 print(out, file=sys.stderr)

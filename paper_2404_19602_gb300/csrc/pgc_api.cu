@@ -30,7 +30,20 @@ Runner *make_runner(int P, int Q, int precision, const HostTables &t, const DevB
     if (P == 1 && Q == 1) return make_runner_1x1(precision, t, b, num_sms);
     if (P == 6 && Q == 6) return make_runner_6x6(precision, t, b, num_sms);
     if (P == 21 && Q == 36) return make_runner_21x36(precision, t, b, num_sms);
+#define PGC_CASE_1D(n) if (P == n && Q == n) return make_runner_1d_##n(precision, t, b, num_sms);
+    PGC_SHAPES_1D(PGC_CASE_1D)
+#undef PGC_CASE_1D
     return nullptr;
+}
+
+static bool shape_compiled(int d, int P, int Q)
+{
+    if ((P == 1 && Q == 1) || (P == 6 && Q == 6) || (P == 21 && Q == 36)) return true;
+    bool one_d = false;
+#define PGC_IS_1D(n) one_d = one_d || (P == n && Q == n);
+    PGC_SHAPES_1D(PGC_IS_1D)
+#undef PGC_IS_1D
+    return d == 1 && one_d;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -490,9 +503,9 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     if (c->max_outputs < 1) return bad("max_outputs must be >= 1");
     L->d = dims_of(*c, &L->P, &L->Q);
     if (L->d > 0 && c->quad_per_dim < c->degree_M + 1) return bad("quad_per_dim must be >= degree_M + 1 (exact projection)");
-    const bool shape_ok = (L->P == 1 && L->Q == 1) || (L->P == 6 && L->Q == 6) || (L->P == 21 && L->Q == 36);
-    if (!shape_ok) {
-        *msg = "compiled (P,Q) shapes are (1,1), (6,6), (21,36); got (" + std::to_string(L->P) + "," + std::to_string(L->Q) + ")";
+    if (!shape_compiled(L->d, L->P, L->Q)) {
+        *msg = "compiled (P,Q) shapes are (1,1), (6,6), (21,36) and, with one random input, (M+1,M+1) for "
+               "M = 1, 2, 3, 4, 6, 8, 10, 12, 15, 20, 25, 30; got (" + std::to_string(L->P) + "," + std::to_string(L->Q) + ")";
         return PGC_EUNSUPPORTED;
     }
     const int64_t N = c->n_particles;
@@ -652,11 +665,11 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     ctx->obs_out = ctx->obs_part + (size_t)kObsGrid * kObsZ * 3;
     ctx->rec_len = L.rec_len;
     ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
+    if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
     // the fused step overlaps the collider work with the streaming work.  For 36 nodes the
     // collider work is itself throughput-bound (many chains per lane group) and, fused, holds
     // most resident blocks for the whole launch: measured slower, so off by default there
     ctx->pipeline = (ctx->run->fused() && L.P * L.Q <= 64) ? 1 : 0;
-    if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
 
     cudaStream_t s = ctx->stream;
     if ((e = cudaMemsetAsync(d_scratch, 0, L.scratch, s)) != cudaSuccess ||

@@ -62,9 +62,9 @@ struct Nodes {
     // a1[q1][h1] = psi_h1(z1_q1), b2[q2][h2] = psi_h2(z2_q2)
     R a1[36], b2[36];
     // FP32: the same weights as pairs (w, w), the operand of the two-lane FMA that reconstructs
-    // the x and y components together (unused in FP64)
-    unsigned long long psi2[TensorShape<P, Q>::value ? 1 : Q * P];
-    unsigned long long wpsi2[TensorShape<P, Q>::value ? 1 : Q * P];
+    // the x and y components together (one unused entry in FP64)
+    unsigned long long psi2[(TensorShape<P, Q>::value || sizeof(R) == 8) ? 1 : Q * P];
+    unsigned long long wpsi2[(TensorShape<P, Q>::value || sizeof(R) == 8) ? 1 : Q * P];
     unsigned long long a1_2[36], b2_2[36];
 };
 
@@ -236,7 +236,8 @@ __device__ __forceinline__ void recon_all(const Nodes<P, Q, R> &nd, const R cx[P
             }
         }
     } else {
-#pragma unroll
+        // (large one-dimensional shapes: a rolled node loop keeps the code size in check)
+#pragma unroll (P * Q <= 64 ? Q : 1)
         for (int q = 0; q < Q; ++q) {
             R kx, ky;
             recon_node(nd, q, cx, cy, kx, ky);
@@ -398,7 +399,7 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
             maybe = screen_maybe(ph, nd, kkmax, r.x);
             if (!maybe) {
                 finished[e] = true;
-#pragma unroll
+#pragma unroll ((P * Q <= 64 || TensorShape<P, Q>::value) ? Q : 1)
                 for (int q = 0; q < Q; ++q) {
                     if (rl[q] < 0) { ++oog; continue; }
                     const int r = rl[q] >> 16, l = rl[q] & 0xffff;
@@ -580,8 +581,8 @@ __device__ __forceinline__ bool group_any(bool b, unsigned mask)
 // Shared-memory transpose reduction of the projection for groups of a whole warp: per warp, 32
 // rows of 2P partial sums (row stride 2P + 1, odd, so that the column reads are conflict-free)
 // and the 2P totals.
-template <int P, int Q, typename R> struct ProjRed {
-    static constexpr bool value = GroupOf<Q>::G == 32 && sizeof(R) == 4;
+template <int P, int Q, typename R> struct ProjRed {   // (its area fits the static shared memory up to P = 21)
+    static constexpr bool value = GroupOf<Q>::G == 32 && sizeof(R) == 4 && P <= 21;
     static constexpr int stride = 2 * P + 1;
     static constexpr int warp_elems = 32 * stride + 2 * P;
 };
@@ -968,14 +969,16 @@ struct InitArgs {
     double wpsi[Q * P];
     double eps0[Q];
     double mu, kT, hvF;
+    int64_t N, ld;
+    uint32_t key0, key1, stream_id;
 };
 
 template <int P, int Q, typename R>
 __global__ void __launch_bounds__(128)
-k_init(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ InitArgs<P, Q> ia)
+k_init(const __grid_constant__ InitArgs<P, Q> ia, R *khat)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
-        const U4 r = philox4x32_10((uint32_t)i, a.stream_id, 0u, 0x10000u, a.key0, a.key1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ia.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const U4 r = philox4x32_10((uint32_t)i, ia.stream_id, 0u, 0x10000u, ia.key0, ia.key1);
         const double ue = u01<double>(r.x), uth = u01<double>(r.y);
         double s, c;
         sincos(2.0 * kPi * uth, &s, &c);
@@ -997,8 +1000,8 @@ k_init(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ Init
         }
 #pragma unroll
         for (int h = 0; h < P; ++h) {
-            a.khat[(int64_t)h * a.ld + i] = (R)hx[h];
-            a.khat[(int64_t)(P + h) * a.ld + i] = (R)hy[h];
+            khat[(int64_t)h * ia.ld + i] = (R)hx[h];
+            khat[(int64_t)(P + h) * ia.ld + i] = (R)hy[h];
         }
     }
 }

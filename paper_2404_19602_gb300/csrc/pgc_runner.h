@@ -93,6 +93,13 @@ Runner *make_runner(int P, int Q, int precision, const HostTables &t, const DevB
 Runner *make_runner_1x1(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
 Runner *make_runner_6x6(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
 Runner *make_runner_21x36(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
+// One-dimensional shapes P = Q = M + 1 beyond the default M = 5 (degrees M = 1..30 of the
+// stochastic-Galerkin error study, Test 3 of Sec. 5): time-step kernels only, no batch or
+// adjoint kernels.  pgc_inst_1d.cu is compiled once per entry with -DPGC_1D_P=<P>.
+#define PGC_SHAPES_1D(X) X(2) X(3) X(4) X(5) X(7) X(9) X(11) X(13) X(16) X(21) X(26) X(31)
+#define PGC_DECL_RUNNER_1D(n) Runner *make_runner_1d_##n(int precision, const HostTables &t, const DevBuffers &b, int num_sms);
+PGC_SHAPES_1D(PGC_DECL_RUNNER_1D)
+#undef PGC_DECL_RUNNER_1D
 
 struct BatchCase;
 struct BatchScratch;
@@ -107,7 +114,7 @@ AdjRunner *make_adj_runner(int P, int Q, int precision, const HostTables &t, con
                            int num_sms);
 
 // Bytes reserved for the device copy of the node tables (the largest compiled shape fits).
-constexpr size_t kTableBytes = 16384;
+constexpr size_t kTableBytes = 32768;
 
 // Launch accounting (every kernel launch of the library increments it).
 void count_launch(uint64_t n = 1);

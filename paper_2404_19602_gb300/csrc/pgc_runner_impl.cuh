@@ -39,7 +39,7 @@ public:
             std::memcpy(&u, &f, 4);
             return ((unsigned long long)u << 32) | u;
         };
-        if constexpr (!TensorShape<P, Q>::value)
+        if constexpr (!TensorShape<P, Q>::value && sizeof(R) == 4)
             for (int i = 0; i < Q * P; ++i) { nd.psi2[i] = pair(t.psi[i]); nd.wpsi2[i] = pair(t.wpsi[i]); }
         for (int i = 0; i < 36; ++i) { nd.a1_2[i] = pair((double)nd.a1[i]); nd.b2_2[i] = pair((double)nd.b2[i]); }
         args_.khat = static_cast<R *>(b.state);
@@ -62,6 +62,11 @@ public:
         init_.mu = t.mu;
         init_.kT = t.kT;
         init_.hvF = t.hvF;
+        init_.N = b.N;
+        init_.ld = b.ld;
+        init_.key0 = b.key0;
+        init_.key1 = b.key1;
+        init_.stream_id = b.stream_id;
         // phase-1 grid: enough resident blocks to fill the GPU, PPT particles per thread; the
         // shared-memory histogram window needs every cell of a window to receive < 2^16 counts
         // from one block, and a window that lies inside the grid
@@ -99,7 +104,7 @@ public:
     cudaError_t init_sample(cudaStream_t s) override
     {
         int blocks = (int)std::min<int64_t>((b_.N + 127) / 128, 8192);
-        k_init<P, Q, R><<<blocks, 128, 0, s>>>(args_, init_);
+        k_init<P, Q, R><<<blocks, 128, 0, s>>>(init_, args_.khat);
         count_launch();
         return cudaGetLastError();
     }

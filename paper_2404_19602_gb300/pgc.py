@@ -347,7 +347,9 @@ class Simulation:
         self.P, self.Q = sz["P"], sz["Q"]
         self.N = int(self.cfg.n_particles)
         self.Nk = int(self.cfg.Nk)
-        self.d = int(self.cfg.eps0_eV.lo != self.cfg.eps0_eV.hi) + int(self.cfg.Ex_Vcm.lo != self.cfg.Ex_Vcm.hi)
+        c = self.cfg
+        eps_random = (c.width_nm.lo != c.width_nm.hi) if c.eps0_law == PGC_EPS0_WIDTH else (c.eps0_eV.lo != c.eps0_eV.hi)
+        self.d = int(eps_random) + int(c.Ex_Vcm.lo != c.Ex_Vcm.hi)   # number of random inputs
         self.max_outputs = max_outputs
         dev = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)

@@ -62,6 +62,17 @@ TEST2_FIELD_1E6 = _w(name="test2_W7nm_E4-6kVcm_epsF0.4_M5_N1e6_fp32", W_lo=7.0, 
                      Ex_lo=4000.0, Ex_hi=6000.0, M=5, Q1=6, N=1_000_000, dt_fs=2.5, steps=1200,
                      precision="fp32")
 
+#: Test 3 (Sec. 5), the stochastic-Galerkin error study: the two Test 2 scenarios with 1e4
+#: particles and eps_F 0.4 eV, dt 2.5 fs, errors at 0.1, 0.5 and 1 ps (40, 200, 400 steps) for
+#: degrees M = 0..25 against M_ref = 30 (the degree is set per run).
+TEST3_WIDTH_1E4 = _w(name="test3_W6.5-7.5nm_E5kVcm_epsF0.4_N1e4_fp32", W_lo=6.5, W_hi=7.5,
+                     Ex_lo=5000.0, Ex_hi=5000.0, M=5, Q1=6, N=10_000, dt_fs=2.5, steps=400,
+                     precision="fp32")
+TEST3_FIELD_1E4 = _w(name="test3_W7nm_E4-6kVcm_epsF0.4_N1e4_fp32", W_lo=7.0, W_hi=7.0,
+                     Ex_lo=4000.0, Ex_hi=6000.0, M=5, Q1=6, N=10_000, dt_fs=2.5, steps=400,
+                     precision="fp32")
+TEST3_TIMES_STEPS = (40, 200, 400)
+
 
 def sweep64(seed: int = 1, n_lo: float = 1e5, n_hi: float = 4e6, steps: int = 3000):
     """64 cases: field 1..20 kV/cm (8 values) x width 0.02..0.2 eV (8 values) of a band-gap

@@ -65,13 +65,23 @@ def test_invalid_configs_are_rejected(lib, field, value):
     assert lib.pgc_last_error(None)
 
 
-def test_uncompiled_shape_is_unsupported(lib):
+@pytest.mark.parametrize("M,quad", [(7, 8), (3, 5), (31, 32)])
+def test_uncompiled_shape_is_unsupported(lib, M, quad):
     cfg = pgc.pgc_config_default()
     cfg.eps0_eV.lo, cfg.eps0_eV.hi = 0.05, 0.15
-    cfg.degree_M, cfg.quad_per_dim = 3, 4
+    cfg.degree_M, cfg.quad_per_dim = M, quad
     with pytest.raises(pgc.PgcError) as e:
         pgc.pgc_query_sizes(cfg)
-    assert e.value.status == pgc.PGC_EUNSUPPORTED
+    assert e.value.status in (pgc.PGC_EUNSUPPORTED, pgc.PGC_EINVAL)
+
+
+@pytest.mark.parametrize("M", [0, 1, 2, 3, 4, 5, 6, 8, 10, 12, 15, 20, 25, 30])
+def test_one_dimensional_degrees_are_compiled(lib, M):
+    cfg = pgc.pgc_config_default()
+    cfg.eps0_eV.lo, cfg.eps0_eV.hi = 0.05, 0.15
+    cfg.degree_M, cfg.quad_per_dim = M, M + 1
+    s = pgc.pgc_query_sizes(cfg)
+    assert s["P"] == s["Q"] == M + 1
 
 
 def test_init_rejects_null_buffers(lib):
