@@ -35,7 +35,7 @@ from paper_2404_19602_gb300 import workloads as W  # noqa: E402
 WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None,
              "adjoint": W.ADJOINT_1E6,
              "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64"),
-             "sg_error": W.TEST3_WIDTH_1E4}
+             "sg_error": W.TEST3_WIDTH_1E4, "mc_compare": W.TEST3_WIDTH_1E4}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -53,7 +53,9 @@ def parse():
                          "inputs), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
                          "reverse sweep of the steady-current sensitivities, 1e6 particles), gap_uq_fp64 "
                          "(the gap_uq ensemble in the FP64 mode), sg_error (the stochastic-Galerkin error "
-                         "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles)")
+                         "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles), mc_compare "
+                         "(Test 4: MC-sG against Algorithm 1 at sampled inputs, 5e4 particles, reference 5e6 "
+                         "particles at degree 30)")
     ap.add_argument("--fd-check", action="store_true",
                     help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
@@ -404,6 +406,61 @@ def run_sg_error(args, pgc, torch, dev, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_mc_compare(args, pgc, torch, dev, rank, world):
+    """Test 4 (Sec. 5): one step = the error of E_z[V_x] at 0.5 ps (200 steps of 2.5 fs) against an
+    sG reference (5e6 particles, degree 30) of MC-sG with 5e4 particles at degrees 0..10 and of
+    MC-MC with 5e4 particles per sample at 1..256 samples (the samples in one batch), uncertain
+    width.  The metric counts the particle-steps of all runs over the wall time of the step
+    (context creation and initial sampling included)."""
+    from paper_2404_19602_gb300 import sg_error as SG
+
+    p = rank_workload(W.TEST3_WIDTH_1E4, rank)
+    steps, N, N_ref, M_ref = 200, 50_000, 5_000_000, 30
+    degrees, samples = (0, 1, 2, 3, 4, 5, 6, 8, 10), (1, 2, 4, 8, 16, 32, 64, 128, 256)
+    ps = steps * (N_ref + N * len(degrees) + N * sum(samples))
+
+    def one():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = SG.mc_comparison(p, degrees, samples, N, N_ref, M_ref, steps)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    for _ in range(args.warmup):
+        one()
+    launches0 = pgc.pgc_launch_count()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    res = [one() for _ in range(args.steps)]
+    clk = clocks.stop()
+    launches = pgc.pgc_launch_count() - launches0
+    wall = max_over_ranks(sum(r[0] for r in res), dev)
+    r = res[-1][1]
+    if rank == 0:
+        value = ps * world * args.steps / wall
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "test4_mcsg_vs_mcmc_W6.5-7.5nm_E5kVcm_t0.5ps_N5e4_ref5e6_M30_fp32",
+                       "particle_steps_per_step": ps, "timing": "wall clock of the whole step",
+                       "l2": "not flushed: the runs follow one another; the 1.2 GB reference state exceeds L2"},
+            "roofline": None,
+            "roofline_note": "a mix of 20 runs of different shapes; the per-kernel rooflines are those of the "
+                             "gap_uq and gap_field lines",
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "the value is already wall clock through the public API; initial states are sampled "
+                            "on the device"},
+            "mc_compare": {"t_ps": steps * p["dt_fs"] / 1000.0, "ref_vx_ms": r["ref_vx"],
+                           "mc_sg": {"M": list(degrees), "cost_per_particle": [(M + 1) ** 2 for M in degrees],
+                                     "err_vx_ms": [r["sg"][M] for M in degrees]},
+                           "mc_mc": {"M2": list(samples), "cost_per_particle": list(samples),
+                                     "err_vx_ms": [r["mc"][M2] for M2 in samples]}},
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -427,8 +484,8 @@ def main():
     from paper_2404_19602_gb300 import build as B
 
     B.build()
-    if args.workload in ("sweep", "adjoint", "sg_error"):
-        {"sweep": run_sweep, "adjoint": run_adjoint, "sg_error": run_sg_error}[args.workload](
+    if args.workload in ("sweep", "adjoint", "sg_error", "mc_compare"):
+        {"sweep": run_sweep, "adjoint": run_adjoint, "sg_error": run_sg_error, "mc_compare": run_mc_compare}[args.workload](
             args, pgc, torch, dev, rank, world)
         if world > 1:
             dist.destroy_process_group()

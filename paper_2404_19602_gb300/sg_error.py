@@ -1,4 +1,5 @@
-"""The stochastic-Galerkin error study of Test 3 (Sec. 5) over the public API.
+"""The stochastic-Galerkin error study of Test 3 (Sec. 5) and the comparison with Monte Carlo
+sampling of the random input of Test 4, over the public API.
 
 For one random input (the ribbon width, or the field), runs of increasing gPC degree M are
 compared with a reference degree M_ref at fixed times t through the energy E(t, z):
@@ -58,3 +59,61 @@ def sg_error(p: dict, degrees, M_ref: int, steps, nz: int = 64, record=None) -> 
     ref = energy_at_times(p, M_ref, steps, z, record)
     return {M: np.sqrt((((energy_at_times(p, M, steps, z, record) - ref) ** 2) * w).sum(axis=1))
             for M in degrees}
+
+
+# ------------------------------------------------------------------------------------------
+# Test 4 (Sec. 5): the particle stochastic-Galerkin method (MC-sG) against Algorithm 1 run at
+# sampled values of the random input (MC-MC), by the error of E_z[V_x] at a fixed time against a
+# large-ensemble, high-degree sG reference.  Cost per particle and time step: (M + 1)^2 for MC-sG
+# (reconstruction and projection over M + 1 coefficients and nodes), M_2 for MC-MC (one
+# deterministic run per sample).
+# ------------------------------------------------------------------------------------------
+def mean_vx_sg(p: dict, M: int, N: int, steps: int) -> float:
+    """E_z[V_x] (m/s) after `steps` time steps of the degree-M particle sG run of N particles
+    (the quadrature mean over the M + 1 nodes, Sec. 4.2)."""
+    s = pgc.Simulation(W.scaled(p, M=M, Q1=M + 1, N=N), max_outputs=4)
+    s.step(steps, steps)
+    v = float(s.moments()["mean"][-1, 0])
+    s.close()
+    return v
+
+
+def deterministic_at(p: dict, z: float) -> dict:
+    """Workload p with its random input fixed at the point z of [-1, 1] (the affine maps of the
+    library: the width for the width law, else the band minimum, else the field)."""
+    t = 0.5 * (z + 1.0)
+    if (p.get("W_lo") or 0.0) > 0.0:
+        if p["W_lo"] != p["W_hi"]:
+            w = p["W_lo"] + (p["W_hi"] - p["W_lo"]) * t
+            return W.scaled(p, W_lo=w, W_hi=w, M=0, Q1=1)
+    elif p["eps0_lo"] != p["eps0_hi"]:
+        e = p["eps0_lo"] + (p["eps0_hi"] - p["eps0_lo"]) * t
+        return W.scaled(p, eps0_lo=e, eps0_hi=e, M=0, Q1=1)
+    if p["Ex_lo"] != p["Ex_hi"]:
+        f = p["Ex_lo"] + (p["Ex_hi"] - p["Ex_lo"]) * t
+        return W.scaled(p, Ex_lo=f, Ex_hi=f, M=0, Q1=1)
+    return W.scaled(p, M=0, Q1=1)
+
+
+def mc_mc_samples(p: dict, M2: int, N: int, steps: int, seed: int = 1) -> np.ndarray:
+    """MC-MC: V_x (m/s) after `steps` time steps of Algorithm 1 at M2 points z_j drawn uniformly
+    (numpy generator `seed`), one independent ensemble of N particles per sample (stream_id j),
+    the samples advanced together by the batched kernels (at most 256 per batch)."""
+    z = np.random.default_rng(seed).uniform(-1.0, 1.0, M2)
+    cases = [W.scaled(deterministic_at(p, float(zj)), N=N, stream_id=j) for j, zj in enumerate(z)]
+    vals = []
+    for c0 in range(0, M2, 256):
+        b = pgc.BatchSimulation(cases[c0:c0 + 256], max_outputs=4)
+        b.step(steps, steps)
+        vals += [float(s.moments()["mean"][-1, 0]) for s in b.sims]
+        b.close()
+    return np.array(vals)
+
+
+def mc_comparison(p: dict, degrees, samples, N: int, N_ref: int, M_ref: int, steps: int, seed: int = 1) -> dict:
+    """Errors |E_z[V_x] - E_z[V_x^ref]| of MC-sG (per degree) and MC-MC (per sample count) with N
+    particles, the reference an sG run of N_ref particles and degree M_ref."""
+    ref = mean_vx_sg(p, M_ref, N_ref, steps)
+    sg = {M: abs(mean_vx_sg(p, M, N, steps) - ref) for M in degrees}
+    mc = {M2: abs(float(mc_mc_samples(p, M2, N, steps, seed).mean()) - ref) for M2 in samples}
+    return {"ref_vx": ref, "sg": sg, "mc": mc}

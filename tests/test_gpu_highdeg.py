@@ -93,7 +93,10 @@ def test_degree_zero_equals_deterministic_run(prec):
     for s in (a, b):
         s.step(50, 25)
     assert np.array_equal(a.state(), b.state())
-    assert np.array_equal(a.moments()["mean"], b.moments()["mean"])
+    # the block partial sums of the moments follow the dynamic tile assignment of the streaming
+    # kernel, so two runs agree to the FP64 accumulation order only
+    ma, mb = a.moments()["mean"], b.moments()["mean"]
+    assert np.allclose(ma, mb, rtol=1e-12, atol=1e-12 * np.abs(mb).max())
     a.close()
     b.close()
 
@@ -167,3 +170,37 @@ def test_sg_error_falls_with_the_degree(base):
     e = sg_error.sg_error(p, (1, 5, 25), 30, W.TEST3_TIMES_STEPS)
     assert np.all(e[25] < e[1] / 4.0), e
     assert np.all(e[5] < e[1]), e
+
+
+def test_mc_mc_batched_samples_equal_standalone_runs():
+    """Test 4's MC-MC samples (Algorithm 1 at sampled inputs, advanced together by the batched
+    kernels) are the standalone deterministic runs at those inputs."""
+    from paper_2404_19602_gb300 import sg_error
+
+    pgc = _pgc()
+    p = W.scaled(W.TEST3_WIDTH_1E4, N=3000)
+    got = sg_error.mc_mc_samples(p, 3, 3000, 30, seed=5)
+    z = np.random.default_rng(5).uniform(-1.0, 1.0, 3)
+    for j, zj in enumerate(z):
+        q = W.scaled(sg_error.deterministic_at(p, float(zj)), stream_id=j)
+        assert q["W_lo"] == q["W_hi"] == pytest.approx(6.5 + 0.5 * (zj + 1.0))
+        s = pgc.Simulation(q, max_outputs=4)
+        s.step(30, 30)
+        # same trajectories; the moment sums group the particles differently in the batch
+        assert s.moments()["mean"][-1, 0] == pytest.approx(got[j], rel=1e-5)
+        s.close()
+
+
+def test_mc_sg_and_mc_mc_estimates_agree():
+    """E_z[V_x] at 0.25 ps by MC-sG (degree 5, 2e5 particles) and by MC-MC (64 samples of 2e4
+    particles) agree within four standard errors (sample spread of MC-MC; particle noise of the
+    sG ensemble bounded by v_F / sqrt(N) since |v_x| <= v_F)."""
+    from paper_2404_19602_gb300 import sg_error
+
+    p = W.TEST3_WIDTH_1E4
+    sg = sg_error.mean_vx_sg(p, 5, 200_000, 100)
+    v = sg_error.mc_mc_samples(p, 64, 20_000, 100, seed=2)
+    se = v.std(ddof=1) / np.sqrt(v.size)
+    tol = 4.0 * np.sqrt(se ** 2 + 1e12 / 200_000)
+    assert abs(sg - v.mean()) <= tol, (sg, v.mean(), tol)
+    assert abs(sg) > 10 * tol / 4.0          # a drift well resolved at this time
