@@ -59,6 +59,7 @@ class _Cfg(C.Structure):
         ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
         ("n_theta", C.c_int32), ("max_coll", C.c_int32),
         ("eps0_law", C.c_int32), ("W_lo", C.c_double), ("W_hi", C.c_double),
+        ("splitting", C.c_int32),
     ]
 
 
@@ -131,7 +132,8 @@ def _u32p(a):
 DEFAULTS = dict(T_K=300.0, eps_F=0.4, eps0_lo=0.1, eps0_hi=0.1, Ex_lo=5000.0, Ex_hi=5000.0,
                 mech_mask=ALL_MECH, alpha=0.1, Nk=240, Lk_hvF=5.0, M=5, Q1=6, N=1000,
                 dt_fs=1.0, seed=1, stream_id=0, pauli_norm=PAULI_INITIAL_MAX,
-                final_state=FS_PAPER, n_theta=64, max_coll=32, eps0_law=0, W_lo=0.0, W_hi=0.0)
+                final_state=FS_PAPER, n_theta=64, max_coll=32, eps0_law=0, W_lo=0.0, W_hi=0.0,
+                splitting=0)
 
 
 def make_cfg(params: dict) -> _Cfg:

@@ -26,6 +26,10 @@
  *   full step ............... conservation, positivity, zero-field symmetry, stationarity of the
  *                             Maxwellian, collision-count statistics, brute-force z sampling of
  *                             the Galerkin mean/variance, degenerate interval = deterministic run.
+ *   Strang splitting ........ without the Pauli test: the Lie run from the initial state moved by
+ *                             half a drift, moved back by half a drift (the two schemes differ by
+ *                             that conjugation); ballistic closed form; second-order agreement
+ *                             of the drift-only observables.
  *                             Beyond these properties, the scattering trajectory itself is
  *                             "parity unpinned" (no published trajectory exists).
  */
@@ -78,6 +82,10 @@
    width, eps0 = pi hbar vF / W (Sec. 2), with W spread over an interval (Test 2) */
 #define ORC_EPS0_AFFINE 0
 #define ORC_EPS0_WIDTH 1
+/* Time splitting of Sec. 3: Lie, f^{n+1} = C_dt(T_dt(f^n)) (the paper's scheme), or Strang,
+ * f^{n+1} = T_{dt/2}(C_dt(T_{dt/2}(f^n))), the second-order splitting the paper names as possible. */
+#define ORC_SPLIT_LIE 0
+#define ORC_SPLIT_STRANG 1
 
 typedef struct {
     double T_K;               /* lattice = initial Fermi-Dirac temperature */
@@ -100,6 +108,7 @@ typedef struct {
     int32_t max_coll;         /* safety cap of collisions per particle and step */
     int32_t eps0_law;         /* ORC_EPS0_AFFINE or ORC_EPS0_WIDTH */
     double W_lo, W_hi;        /* ribbon width interval, nm (ORC_EPS0_WIDTH) */
+    int32_t splitting;        /* ORC_SPLIT_LIE (the paper's scheme) or ORC_SPLIT_STRANG */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -750,8 +759,8 @@ int orc_init(void *st, const double *h_khat)
 /* Returns 1 if the state changed.                                                            */
 /* ------------------------------------------------------------------------------------------ */
 static int collide_node(const orc_state *S, int q, double Gt, const double *g, double s, double eta,
-                        double uth, const uint32_t *Hn, const uint32_t *Nmax, double *kx, double *ky,
-                        int64_t *rej)
+                        double uth, const uint32_t *Hn, const uint32_t *Nmax, double shift, double *kx,
+                        double *ky, int64_t *rej)
 {
     const orc_cfg *c = &S->cfg;
     double target = s * Gt;
@@ -798,10 +807,11 @@ static int collide_node(const orc_state *S, int q, double Gt, const double *g, d
     }
     /* Pauli test against the previous-step distribution (Eq. (22)/(27)).  Reading: H^n was
      * counted on the fixed grid before the drift; the grid moves with the drift (Lagrangian,
-     * Sec. 3), so the post-drift candidate k' is looked up at cell(k' + (e/hbar) E dt).  Cells
+     * Sec. 3), so the post-drift candidate k' is looked up at cell(k' + shift) with shift the
+     * drift applied since H^n was counted: (e/hbar) E dt (Lie), half of it (Strang).  Cells
      * outside [-Lk,Lk]^2 have f = 0 (zero boundary condition). */
     if (c->pauli_norm != ORC_PAULI_OFF) {
-        int64_t cell = cell_of(S, nkx + S->dq[q], nky);
+        int64_t cell = cell_of(S, nkx + shift, nky);
         double f = 0.0;
         if (cell >= 0 && Nmax[q] > 0)
             f = (double)Hn[(size_t)q * c->Nk * c->Nk + cell] / (double)Nmax[q];
@@ -827,8 +837,9 @@ static void step_particle(orc_state *S, int64_t i, int64_t n, const uint32_t *Hn
     int64_t N = c->N;
     double kx[1296], ky[1296], g[1296 * 6];
     int64_t att = 0, real = 0, rej = 0, cap = 0;
-    /* drift of the coefficients */
-    for (int h = 0; h < P; ++h) S->khat[((size_t)0 * P + h) * N + i] -= S->dhat[h];
+    const int strang = (c->splitting == ORC_SPLIT_STRANG);
+    /* drift of the coefficients: T_dt, or T_{dt/2} before the collisions (Strang) */
+    for (int h = 0; h < P; ++h) S->khat[((size_t)0 * P + h) * N + i] -= strang ? 0.5 * S->dhat[h] : S->dhat[h];
     recon_particle(S, i, kx, ky);
     /* majorant: Gt = (1+alpha) max_q sum_nu Gamma_nu(k(z_q))  (Eq. (19), Eq. (25)) */
     double Gt = 0.0;
@@ -849,7 +860,8 @@ static void step_particle(orc_state *S, int64_t i, int64_t n, const uint32_t *Hn
         ++att;
         int changed = 0;
         for (int q = 0; q < Q; ++q)
-            changed |= collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, &kx[q], &ky[q], &rej);
+            changed |= collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx,
+                                    strang ? 0.5 * S->dq[q] : S->dq[q], &kx[q], &ky[q], &rej);
         if (changed) ++real;
         /* collisional matrices K1 + K2 (Eqs. (28)-(30)): project the per-node result */
         project_particle(S, i, kx, ky);
@@ -867,6 +879,9 @@ static void step_particle(orc_state *S, int64_t i, int64_t n, const uint32_t *Hn
         orc_draw(c, i, n, cc, u);
         dtc = (Gt > 0.0) ? -log(u[0]) / Gt : INFINITY;
     }
+    /* Strang: the second half of the drift, T_{dt/2} after the collisions */
+    if (strang)
+        for (int h = 0; h < P; ++h) S->khat[((size_t)0 * P + h) * N + i] -= 0.5 * S->dhat[h];
     *att_ += att; *real_ += real; *rej_ += rej; *cap_ += cap;
 }
 
@@ -1226,7 +1241,9 @@ int orc_tangent_run(void *st, int64_t nsteps, int64_t every, int64_t window, dou
 {
     orc_state *S = (orc_state *)st;
     const orc_cfg *c = &S->cfg;
-    if (!S->sampled || S->step != 0 || c->final_state != ORC_FS_PAPER || every < 1) return -1;
+    if (!S->sampled || S->step != 0 || c->final_state != ORC_FS_PAPER || every < 1 ||
+        c->splitting != ORC_SPLIT_LIE)
+        return -1;
     int P = S->P, Q = S->Q;
     int64_t N = c->N;
     double *dk = (double *)calloc((size_t)NTH * 2 * P * N, sizeof(double));
@@ -1316,7 +1333,8 @@ int orc_tangent_run(void *st, int64_t nsteps, int64_t every, int64_t window, dou
                     double target = u[1] * Gt, cum = 0.0;
                     int l = 6;
                     for (int m = 0; m < 6; ++m) { cum += g[q * 6 + m]; if (target < cum) { l = m; break; } }
-                    int changed = collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, &kx[q], &ky[q], &rej);
+                    int changed = collide_node(S, q, Gt, &g[q * 6], u[1], u[2], u[3], Hn, Nmx, S->dq[q], &kx[q],
+                                               &ky[q], &rej);
                     if (changed) {
                         double J[4];
                         fs_jacobian(S, l, k0x, k0y, u[3], J);
