@@ -93,6 +93,15 @@ enum { PGC_FS_PAPER = 0, PGC_FS_EXACT_ENERGY = 1 };
  * between width_nm.lo and .hi and eps0(z) = hbar vF pi / W(z) (not a polynomial in z; the
  * scenario of Test 2, W = (6.5 + z) nm). */
 enum { PGC_EPS0_AFFINE = 0, PGC_EPS0_WIDTH = 1 };
+/* Time splitting of the field drift T and the collisions C (Sec. 3): LIE, one step is
+ * C_dt(T_dt(f)) (the paper's scheme); STRANG, T_{dt/2}(C_dt(T_{dt/2}(f))), the second-order
+ * splitting the paper names as possible.  In the Strang form the Pauli look-up of a candidate
+ * k' is at cell(k' + (e/hbar) E dt / 2) of f^n, and every histogram and observable is that of
+ * the state at the step boundary.  The device state buffer then holds the coefficients of the
+ * state at the step boundary plus half a step's drift (k^n + (e/hbar) E dt / 2, x coefficients);
+ * pgc_get_state / pgc_set_state convert, and the batch and adjoint entry points return
+ * PGC_EUNSUPPORTED for it. */
+enum { PGC_SPLIT_LIE = 0, PGC_SPLIT_STRANG = 1 };
 
 /* counters returned by pgc_counters */
 enum {
@@ -132,6 +141,7 @@ typedef struct {
     int32_t max_outputs;     /* capacity of the moment time series */
     int32_t eps0_law;        /* PGC_EPS0_AFFINE (default) or PGC_EPS0_WIDTH */
     pgc_interval width_nm;   /* ribbon width, nm (WIDTH law; lo > 0) */
+    int32_t splitting;       /* PGC_SPLIT_LIE (default) or PGC_SPLIT_STRANG */
 } pgc_config;
 
 typedef struct pgc_ctx pgc_ctx;

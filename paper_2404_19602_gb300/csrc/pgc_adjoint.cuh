@@ -356,7 +356,7 @@ __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, 
                 final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
                 bool accept = true;
                 if (ph.pauli_mode != 2) {
-                    const int cl = cell_of(ph, nkx + nd.dq[q], nky);
+                    const int cl = cell_of(ph, nd.lkx[q], nkx + nd.dq[q], nky);
                     if (cl >= 0) accept = pauli_accept(a.Hn[(int64_t)q * NN + cl], a.nmax[q], rr.z);
                 }
                 if (accept) l_out[s] = l;
@@ -385,7 +385,7 @@ __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, 
             final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
             bool accept = true;
             if (ph.pauli_mode != 2) {
-                const int cl = cell_of(ph, nkx + nd.dq[q], nky);
+                const int cl = cell_of(ph, nd.lkx[q], nkx + nd.dq[q], nky);
                 if (cl >= 0) accept = pauli_accept(a.Hn[(int64_t)q * NN + cl], a.nmax[q], rr.z);
             }
             if (accept) { kx[s] = nkx; ky[s] = nky; }

@@ -106,6 +106,8 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
     if (!ctx->sampled || ctx->step != 0) return afail(ctx, PGC_EINVAL, "the adjoint starts from the sampled initial state (step 0, no state upload)");
     if (ctx->cfg.eps0_law != PGC_EPS0_AFFINE)
         return afail(ctx, PGC_EUNSUPPORTED, "the adjoint differentiates the affine band-minimum endpoints (PGC_EPS0_AFFINE)");
+    if (ctx->cfg.splitting != PGC_SPLIT_LIE)
+        return afail(ctx, PGC_EUNSUPPORTED, "the adjoint differentiates the Lie splitting (PGC_SPLIT_LIE)");
     if (ctx->t.final_state != PGC_FS_PAPER || ctx->t.pauli_mode == PGC_PAULI_CURRENT_MAX)
         return afail(ctx, PGC_EUNSUPPORTED, "the adjoint supports the paper's final states and the initial-maximum or off Pauli modes");
     if (moments_every < 1 || window_steps < 1 || window_steps > n_steps) return afail(ctx, PGC_EINVAL, "need moments_every >= 1 and 1 <= window_steps <= n_steps");

@@ -259,6 +259,13 @@ static void build_tables(const pgc_config &c, HostTables &t)
         if (std::fabs(t.dhat[h]) <= 1e-13 * dmax) t.dhat[h] = 0.0;
         if (t.dhat[h] != 0.0) t.drift_mask |= (1u << h);
     }
+    t.strang = c.splitting == PGC_SPLIT_STRANG;
+    t.xs.assign(Q, 0.0);
+    t.dhalf.assign(P, 0.0);
+    if (t.strang) {
+        for (int q = 0; q < Q; ++q) t.xs[q] = 0.5 * t.dq[q];
+        for (int h = 0; h < P; ++h) t.dhalf[h] = 0.5 * t.dhat[h];
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -481,6 +488,7 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     auto bad = [&](const char *m) { *msg = m; return PGC_EINVAL; };
     if (!(c->T_K > 0.0)) return bad("T_K must be > 0");
     if (c->eps0_law != PGC_EPS0_AFFINE && c->eps0_law != PGC_EPS0_WIDTH) return bad("eps0_law must be PGC_EPS0_AFFINE or PGC_EPS0_WIDTH");
+    if (c->splitting != PGC_SPLIT_LIE && c->splitting != PGC_SPLIT_STRANG) return bad("splitting must be PGC_SPLIT_LIE or PGC_SPLIT_STRANG");
     if (c->eps0_law == PGC_EPS0_AFFINE && (!(c->eps0_eV.lo > 0.0) || !(c->eps0_eV.hi >= c->eps0_eV.lo)))
         return bad("eps0 interval must satisfy 0 < lo <= hi");
     if (c->eps0_law == PGC_EPS0_WIDTH && (!(c->width_nm.lo > 0.0) || !(c->width_nm.hi >= c->width_nm.lo) || !std::isfinite(c->width_nm.hi)))
@@ -564,6 +572,7 @@ void pgc_config_default(pgc_config *c)
     c->max_outputs = 1024;
     c->eps0_law = PGC_EPS0_AFFINE;
     c->width_nm.lo = c->width_nm.hi = 0.0;
+    c->splitting = PGC_SPLIT_LIE;
 }
 
 pgc_status pgc_query_sizes(const pgc_config *cfg, size_t *state_bytes, size_t *hist_bytes,
@@ -839,12 +848,16 @@ pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat)
     cudaError_t e = cudaMemcpyAsync(tmp, ctx->b.state, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
-    for (int p = 0; p < 2 * P; ++p)
+    for (int p = 0; p < 2 * P; ++p) {
+        const double sh = (p < P) ? ctx->t.dhalf[p] : 0.0;   // Strang: back to the step boundary
         host_parallel(N, [&](int64_t lo, int64_t hi) {
-            for (int64_t i = lo; i < hi; ++i)
-                h_khat[(size_t)p * N + i] = f64 ? ((const double *)tmp)[(size_t)p * ld + i]
-                                                : (double)((const float *)tmp)[(size_t)p * ld + i];
+            for (int64_t i = lo; i < hi; ++i) {
+                const double v = f64 ? ((const double *)tmp)[(size_t)p * ld + i]
+                                     : (double)((const float *)tmp)[(size_t)p * ld + i];
+                h_khat[(size_t)p * N + i] = (sh != 0.0) ? v - sh : v;
+            }
         });
+    }
     return PGC_OK;
 }
 
@@ -862,9 +875,10 @@ pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
     char *tmp = (char *)staging(ctx, bytes);
     if (!tmp) return fail(ctx, PGC_ENOMEM, "pinned staging buffer");
     for (int p = 0; p < 2 * P; ++p) {
+        const double sh = (p < P) ? ctx->t.dhalf[p] : 0.0;   // Strang: half a drift ahead
         host_parallel(N, [&](int64_t lo, int64_t hi) {
             for (int64_t i = lo; i < hi; ++i) {
-                const double v = h_khat[(size_t)p * N + i];
+                const double v = (sh != 0.0) ? h_khat[(size_t)p * N + i] + sh : h_khat[(size_t)p * N + i];
                 if (f64) ((double *)tmp)[(size_t)p * ld + i] = v;
                 else ((float *)tmp)[(size_t)p * ld + i] = (float)v;
             }
@@ -926,8 +940,10 @@ pgc_status pgc_reconstruct_f(pgc_ctx *ctx, const double *h_z, int32_t nz, uint32
                 if (!(h_z[(size_t)j * d + k] >= -1.0 && h_z[(size_t)j * d + k] <= 1.0))
                     return fail(ctx, PGC_EINVAL, "z outside [-1,1]");
         basis_at(d, ctx->cfg.degree_M, d ? &h_z[(size_t)j * d] : nullptr, psi.data());
+        double xs = 0.0;   // Strang: half the drift at z
+        for (int h = 0; h < P; ++h) xs += ctx->t.dhalf[h] * psi[h];
         cudaError_t e = cudaMemsetAsync(ctx->b.recon_hist, 0, cells * 4, ctx->stream);
-        if (e == cudaSuccess) e = ctx->run->hist_at(psi.data(), ctx->b.recon_hist, ctx->stream);
+        if (e == cudaSuccess) e = ctx->run->hist_at(psi.data(), xs, ctx->b.recon_hist, ctx->stream);
         if (e == cudaSuccess) {
             k_hist_max<<<1, 256, 0, ctx->stream>>>(ctx->b.recon_hist, cells, ctx->tmp_max);
             count_launch();
@@ -951,7 +967,7 @@ pgc_status pgc_observe_at(pgc_ctx *ctx, const double *h_z, int32_t nz, double *h
     for (int64_t j = 0; j < (int64_t)nz * d; ++j)
         if (!(h_z[j] >= -1.0 && h_z[j] <= 1.0)) return fail(ctx, PGC_EINVAL, "z outside [-1,1]");
     const HostTables &t = ctx->t;
-    std::vector<double> psi((size_t)kObsZ * P), e0(kObsZ);
+    std::vector<double> psi((size_t)kObsZ * P), e0(kObsZ), xs(kObsZ);
     for (int j0 = 0; j0 < nz; j0 += kObsZ) {
         const int nzc = std::min(kObsZ, nz - j0);
         ObsFin f{};
@@ -961,10 +977,12 @@ pgc_status pgc_observe_at(pgc_ctx *ctx, const double *h_z, int32_t nz, double *h
             // z1 is the band-minimum variable when the band minimum is random
             const double ze = ((d == 1 && t.eps_random) || d == 2) ? z[0] : 0.0;
             e0[l] = eps0_at(ctx->cfg, t.hvF, ze);
+            xs[l] = 0.0;   // Strang: half the drift at z
+            for (int h = 0; h < P; ++h) xs[l] += t.dhalf[h] * psi[(size_t)l * P + h];
             f.n[l] = 2.0 / (kPi * t.hvF * t.hvF) * fd_upper<double>(e0[l], ctx->cfg.eps_F_eV, t.kT) * 1.0e18;
         }
         int g = 0;
-        cudaError_t e = ctx->run->obs_at(psi.data(), e0.data(), nzc, ctx->obs_part, &g, ctx->stream);
+        cudaError_t e = ctx->run->obs_at(psi.data(), e0.data(), xs.data(), nzc, ctx->obs_part, &g, ctx->stream);
         if (e == cudaSuccess) {
             f.scale_v = t.hvF * t.vF_ms / (double)ctx->b.N;
             f.inv_N = 1.0 / (double)ctx->b.N;

@@ -86,6 +86,7 @@ pgc_status check_batch(pgc_ctx *const *ctxs, int32_t n, BatchLayout *L, std::str
             return PGC_EINVAL;
         }
         if (c->step != c0->step) { *msg = "all contexts must be at the same step"; return PGC_EINVAL; }
+        if (a.splitting != PGC_SPLIT_LIE) { *msg = "the batched kernels run the Lie splitting (PGC_SPLIT_LIE)"; return PGC_EUNSUPPORTED; }
         if (c->stream != c0->stream) { *msg = "all contexts must use the same stream"; return PGC_EINVAL; }
         ntot += c->b.N;
         tiles += (c->b.N + pass - 1) / pass;

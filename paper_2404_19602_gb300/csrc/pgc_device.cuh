@@ -120,6 +120,29 @@ __device__ __forceinline__ int cell_of(const Phys<R> &ph, R kx, R ky)
     return cell_rl(ph, kx, ky, r, l) ? r * ph.Nk + l : -1;
 }
 
+// The same cells with the x offset of the grid given per node: lkx = Lk - s counts k on the grid
+// moved by s along x (s = half a step's drift under the Strang splitting; lkx = Lk otherwise,
+// which is the arithmetic of cell_rl).
+template <typename R>
+__device__ __forceinline__ bool cell_rl(const Phys<R> &ph, R lkx, R kx, R ky, int &r, int &l)
+{
+    if constexpr (sizeof(R) == 8) {
+        r = __double2int_rd((kx + lkx) / ph.dk);
+        l = __double2int_rd((ky + ph.Lk) / ph.dk);
+    } else {
+        r = __float2int_rd((kx + lkx) * ph.inv_dk);
+        l = __float2int_rd((ky + ph.Lk) * ph.inv_dk);
+    }
+    return (unsigned)r < (unsigned)ph.Nk && (unsigned)l < (unsigned)ph.Nk;
+}
+
+template <typename R>
+__device__ __forceinline__ int cell_of(const Phys<R> &ph, R lkx, R kx, R ky)
+{
+    int r, l;
+    return cell_rl(ph, lkx, kx, ky, r, l) ? r * ph.Nk + l : -1;
+}
+
 // ------------------------------------------------------------------------------------------
 // Edge integral T(|k|, c) = int_0^{2pi} exp(-beta (cos th' - c)^2) d th' (Appendix A).
 // The paper evaluates it by the trapezoid rule.  For a periodic analytic integrand the

@@ -56,6 +56,8 @@ struct Nodes {
     R dhat[P];       // per-step drift of the x coefficients
     R eps0[Q];       // band minimum at the node
     R dq[Q];         // per-step drift (e/hbar) E(z_q) dt at the node
+    R lkx[Q];        // x offset of the grid at the node: Lk, or Lk - dq/2 (Strang)
+    R xs[Q];         // x shift from the stored state to the state at the step boundary: 0, or dq/2 (Strang)
     R eps0_max;
     uint32_t drift_mask;  // coefficients h with dhat[h] != 0
     // 2-D tensor nodes (P = 21, Q = 36): one-dimensional basis values for sum factorisation,
@@ -392,7 +394,7 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
             R kkmax = (R)0;
             recon_all(nd, cx[e], cy[e], [&](int q, R kx, R ky) {
                 int r, l;
-                rl[q] = cell_rl(ph, kx, ky, r, l) ? ((r << 16) | l) : -1;
+                rl[q] = cell_rl(ph, nd.lkx[q], kx, ky, r, l) ? ((r << 16) | l) : -1;
                 kkmax = fmax(kkmax, knorm2(kx, ky));
             });
             const U4 r = philox4x32_10((uint32_t)i, t.stream_id, t.step, 0u, t.key0, t.key1);
@@ -433,7 +435,7 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
                 if (finished[e]) {
                     R kx, ky, a1, a2, a3;
                     recon_node(nd, q, cx[e], cy[e], kx, ky);
-                    observe(ph, kx, ky, nd.eps0[q], a1, a2, a3);
+                    observe(ph, kx - nd.xs[q], ky, nd.eps0[q], a1, a2, a3);
                     vx += a1; vy += a2; en += a3;
                 }
             vx = warp_sum(vx);
@@ -734,7 +736,7 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             final_state(ph, l, kx[s], ky[s], nd.eps0[q], ang, &nkx, &nky);
             bool accept = true;
             if (ph.pauli_mode != 2) {
-                const int cl = cell_of(ph, nkx + nd.dq[q], nky);
+                const int cl = cell_of(ph, nd.lkx[q], nkx + nd.dq[q], nky);
                 if (cl >= 0) accept = pauli_accept(t.Hcur[(int64_t)q * NN + cl], t.nmax[q], rr.z);
             }
             if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
@@ -771,12 +773,12 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
     for (int s = 0; s < NPL; ++s) {
         const int q = r + s * G;
         if (q >= Q) continue;
-        const int cl = cell_of(ph, kx[s], ky[s]);
+        const int cl = cell_of(ph, nd.lkx[q], kx[s], ky[s]);
         if (cl >= 0) atomicAdd(&t.Hnext[(int64_t)q * NN + cl], 1u);
         else ++cnt.oog;
         if (t.out_step) {
             R vx, vy, e;
-            observe(ph, kx[s], ky[s], nd.eps0[q], vx, vy, e);
+            observe(ph, kx[s] - nd.xs[q], ky[s], nd.eps0[q], vx, vy, e);
             atomicAdd(&t.mom[q * 3 + 0], (double)vx);
             atomicAdd(&t.mom[q * 3 + 1], (double)vy);
             atomicAdd(&t.mom[q * 3 + 2], (double)e);
@@ -793,7 +795,7 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             if (q < Q) {
                 R x, y;
                 recon_at(nd, q, cx, cy, x, y);
-                cl2[s] = cell_of(ph, x, y);
+                cl2[s] = cell_of(ph, nd.lkx[q], x, y);
                 kk = fmax(kk, knorm2(x, y));
             }
         }
@@ -809,7 +811,7 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
                 if (t.out_next) {
                     R x, y, vx, vy, e;
                     recon_node(nd, q, cx, cy, x, y);
-                    observe(ph, x, y, nd.eps0[q], vx, vy, e);
+                    observe(ph, x - nd.xs[q], y, nd.eps0[q], vx, vy, e);
                     atomicAdd(&t.momN[q * 3 + 0], (double)vx);
                     atomicAdd(&t.momN[q * 3 + 1], (double)vy);
                     atomicAdd(&t.momN[q * 3 + 2], (double)e);
@@ -938,9 +940,9 @@ k_observe(const __grid_constant__ StepArgs<P, Q, R> a)
             if (valid) {
                 R kx, ky;
                 recon_node(nd, q, cx, cy, kx, ky);
-                const int cl = cell_of(ph, kx, ky);
+                const int cl = cell_of(ph, nd.lkx[q], kx, ky);
                 if (cl >= 0) atomicAdd(&a.Hnext[(int64_t)q * NN + cl], 1u);
-                observe(ph, kx, ky, nd.eps0[q], vx, vy, e);
+                observe(ph, kx - nd.xs[q], ky, nd.eps0[q], vx, vy, e);
             }
             vx = warp_sum(vx);
             vy = warp_sum(vy);
@@ -969,6 +971,8 @@ struct InitArgs {
     double wpsi[Q * P];
     double eps0[Q];
     double mu, kT, hvF;
+    double dhalf[P];   // Strang: the stored state leads by half a drift (x coefficients)
+    int32_t strang;
     int64_t N, ld;
     uint32_t key0, key1, stream_id;
 };
@@ -1000,7 +1004,7 @@ k_init(const __grid_constant__ InitArgs<P, Q> ia, R *khat)
         }
 #pragma unroll
         for (int h = 0; h < P; ++h) {
-            khat[(int64_t)h * ia.ld + i] = (R)hx[h];
+            khat[(int64_t)h * ia.ld + i] = (R)(ia.strang ? hx[h] + ia.dhalf[h] : hx[h]);
             khat[(int64_t)(P + h) * ia.ld + i] = (R)hy[h];
         }
     }
@@ -1010,6 +1014,7 @@ k_init(const __grid_constant__ InitArgs<P, Q> ia, R *khat)
 template <int P, int Q, typename R>
 struct ReconArgs {
     double psi[P];
+    R lkx;   // x offset of the grid at z (Lk, or Lk minus half the drift at z under Strang)
 };
 
 template <int P, int Q, typename R>
@@ -1024,7 +1029,7 @@ k_hist_at(const __grid_constant__ StepArgs<P, Q, R> a, const __grid_constant__ R
             kx += a.khat[(int64_t)h * a.ld + i] * (R)z.psi[h];
             ky += a.khat[(int64_t)(P + h) * a.ld + i] * (R)z.psi[h];
         }
-        const int cl = cell_of(a.ph, kx, ky);
+        const int cl = cell_of(a.ph, z.lkx, kx, ky);
         if (cl >= 0) atomicAdd(&out[cl], 1u);
     }
 }
@@ -1054,6 +1059,7 @@ struct ObsArgs {
     R hvF2;
     R psi[kObsZ * P];   // basis at each point; zero rows for unused lanes
     R e0sq[kObsZ];      // eps0(z)^2; 1 for unused lanes
+    R xs[kObsZ];        // x shift of the state at the point (Strang; else 0)
 };
 
 template <typename R> struct Pair;
@@ -1074,6 +1080,7 @@ k_obs_at(const __grid_constant__ ObsArgs<P, R> a, double *part)
 #pragma unroll
     for (int h = 0; h < P; ++h) ps[h] = a.psi[lane * P + h];
     const R e0sq = a.e0sq[lane];
+    const R xs = a.xs[lane];
     double ax = 0.0, ay = 0.0, ae = 0.0;
     const int64_t ntiles = (a.N + T - 1) / T;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1101,6 +1108,7 @@ k_obs_at(const __grid_constant__ ObsArgs<P, R> a, double *part)
                     s = f2_fma(f2_pack(c.x, c.y), w.v, s);
                 }
                 f2_unpack(s, kx, ky);
+                kx -= xs;
             } else {
                 kx = (R)0;
                 ky = (R)0;
@@ -1110,6 +1118,7 @@ k_obs_at(const __grid_constant__ ObsArgs<P, R> a, double *part)
                     kx += c.x * ps[h];
                     ky += c.y * ps[h];
                 }
+                kx -= xs;
             }
             const R eps = rsqrt_<R>(a.hvF2 * (kx * kx + ky * ky) + e0sq);
             const R ie = (R)1 / eps;

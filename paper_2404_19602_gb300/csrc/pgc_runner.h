@@ -22,6 +22,12 @@ struct HostTables {
     std::vector<double> dq;     // [Q] (e/hbar) E dt, nm^-1
     std::vector<double> nq;     // [Q] electron density, m^-2
     std::vector<double> dhat;   // [P]
+    // Strang splitting: the stored state leads the state at the step boundary by half a drift;
+    // xs[q] = dq[q] / 2 is subtracted from node x values before cells and observables, and
+    // dhalf[h] = dhat[h] / 2 from the x coefficients on the way out (all zero for Lie)
+    bool strang = false;
+    std::vector<double> xs;     // [Q]
+    std::vector<double> dhalf;  // [P]
     double eps0_max = 0.0;
     uint32_t drift_mask = 0;
     // physics in eV, fs, nm
@@ -79,12 +85,14 @@ public:
     virtual bool fused() const = 0;   // step_fused is available for this shape
     // copy the node tables to DevBuffers::tables (after the scratch buffer was cleared)
     virtual cudaError_t upload_tables(cudaStream_t s) = 0;
-    // histogram at one arbitrary z (psi of length P, FP64) into out [Nk*Nk]
-    virtual cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) = 0;
-    // block partials of the observables at nzc <= 32 arbitrary points (psi [nzc][P] and the band
-    // minima eps0 [nzc], FP64) into part [blocks][32][3]; *blocks receives the block count
-    virtual cudaError_t obs_at(const double *psi, const double *eps0, int nzc, double *part, int *blocks,
-                               cudaStream_t s) = 0;
+    // histogram at one arbitrary z (psi of length P, FP64; xs: x shift of the state at z, nonzero
+    // for the Strang splitting) into out [Nk*Nk]
+    virtual cudaError_t hist_at(const double *psi, double xs, uint32_t *out, cudaStream_t s) = 0;
+    // block partials of the observables at nzc <= 32 arbitrary points (psi [nzc][P], the band
+    // minima eps0 [nzc] and the x shifts xs [nzc], FP64) into part [blocks][32][3]; *blocks
+    // receives the block count
+    virtual cudaError_t obs_at(const double *psi, const double *eps0, const double *xs, int nzc, double *part,
+                               int *blocks, cudaStream_t s) = 0;
 };
 
 // Factories, one per compiled (P, Q) shape; precision 0 = FP32, 1 = FP64.  nullptr if the

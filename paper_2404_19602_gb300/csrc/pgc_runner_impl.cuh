@@ -21,7 +21,12 @@ public:
         auto &nd = args_.nd;
         for (int i = 0; i < Q * P; ++i) { nd.psi[i] = (R)t.psi[i]; nd.wpsi[i] = (R)t.wpsi[i]; }
         for (int h = 0; h < P; ++h) nd.dhat[h] = (R)t.dhat[h];
-        for (int q = 0; q < Q; ++q) { nd.eps0[q] = (R)t.eps0[q]; nd.dq[q] = (R)t.dq[q]; }
+        for (int q = 0; q < Q; ++q) {
+            nd.eps0[q] = (R)t.eps0[q];
+            nd.dq[q] = (R)t.dq[q];
+            nd.lkx[q] = (R)(t.Lk - t.xs[q]);   // Lie: the grid's Lk itself
+            nd.xs[q] = (R)t.xs[q];
+        }
         nd.eps0_max = (R)t.eps0_max;
         if constexpr (TensorShape<P, Q>::value) {
             // psi(q1,q2) = a_h1(z1_q1) b_h2(z2_q2) with a_0 = b_0 = 1
@@ -62,6 +67,8 @@ public:
         init_.mu = t.mu;
         init_.kT = t.kT;
         init_.hvF = t.hvF;
+        for (int h = 0; h < P; ++h) init_.dhalf[h] = t.dhalf[h];
+        init_.strang = t.strang ? 1 : 0;
         init_.N = b.N;
         init_.ld = b.ld;
         init_.key0 = b.key0;
@@ -230,17 +237,18 @@ public:
         return e;
     }
 
-    cudaError_t hist_at(const double *psi, uint32_t *out, cudaStream_t s) override
+    cudaError_t hist_at(const double *psi, double xs, uint32_t *out, cudaStream_t s) override
     {
         ReconArgs<P, Q, R> z;
         for (int h = 0; h < P; ++h) z.psi[h] = psi[h];
+        z.lkx = (R)(t_.Lk - xs);
         int blocks = (int)std::min<int64_t>((b_.N + 255) / 256, 4096);
         k_hist_at<P, Q, R><<<blocks, 256, 0, s>>>(args_, z, out);
         count_launch();
         return cudaGetLastError();
     }
 
-    cudaError_t obs_at(const double *psi, const double *eps0, int nzc, double *part, int *blocks,
+    cudaError_t obs_at(const double *psi, const double *eps0, const double *xs, int nzc, double *part, int *blocks,
                        cudaStream_t s) override
     {
         ObsArgs<P, R> o;
@@ -252,6 +260,7 @@ public:
             for (int h = 0; h < P; ++h) o.psi[l * P + h] = (l < nzc) ? (R)psi[(size_t)l * P + h] : (R)0;
             const R e = (l < nzc) ? (R)eps0[l] : (R)1;
             o.e0sq[l] = e * e;   // as the node observables square the band minimum
+            o.xs[l] = (l < nzc) ? (R)xs[l] : (R)0;
         }
         constexpr int T = ObsTile<P, R>::value;
         const int g = (int)std::min<int64_t>((b_.N + T - 1) / T, kObsGrid);

@@ -49,11 +49,12 @@ class pgc_config(C.Structure):
         ("seed", C.c_uint64), ("stream_id", C.c_uint32),
         ("precision", C.c_int32), ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
         ("n_theta_edge", C.c_int32), ("max_collisions", C.c_int32), ("max_outputs", C.c_int32),
-        ("eps0_law", C.c_int32), ("width_nm", pgc_interval),
+        ("eps0_law", C.c_int32), ("width_nm", pgc_interval), ("splitting", C.c_int32),
     ]
 
 
 PGC_EPS0_AFFINE, PGC_EPS0_WIDTH = 0, 1
+PGC_SPLIT_LIE, PGC_SPLIT_STRANG = 0, 1
 
 
 _vp, _dp, _u32p, _u64p, _i64p = (C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
@@ -325,6 +326,7 @@ def config_from(params: dict, max_outputs: int = 1024) -> pgc_config:
         c.eps0_law = PGC_EPS0_WIDTH
         c.width_nm.lo = p["W_lo"]
         c.width_nm.hi = p.get("W_hi", p["W_lo"])
+    c.splitting = p.get("splitting", c.splitting)   # PGC_SPLIT_LIE (0) or PGC_SPLIT_STRANG (1)
     return c
 
 

@@ -9,7 +9,8 @@ ends = deterministic), Ex_lo/Ex_hi (V/cm), mech_mask (bit set of the rate vector
 63 = all), alpha (Eq. (19)), Nk and Lk_hvF (grid of Sec. 3), M (gPC degree), Q1 (Gauss nodes per
 random dimension), N (particles), dt_fs, seed (Philox key), stream_id, pauli_norm
 (0 = maximum of the initial histogram, 1 = current maximum, 2 = off), final_state (0 = the
-paper's |k| -+ omega/vF, 1 = exact energy), n_theta (trapezoid points of the edge integral).
+paper's |k| -+ omega/vF, 1 = exact energy), n_theta (trapezoid points of the edge integral),
+splitting (0 = the paper's Lie splitting, 1 = Strang).
 
 A band gap E_g maps to eps0 = E_g / 2 (the conduction-band minimum of the gapped Dirac cone).
 With W_lo/W_hi (nm) present the ribbon width is the input instead: W(z) spreads affinely over
@@ -21,7 +22,7 @@ import numpy as np
 
 #: Sec. 5 simulation parameters (grid, self-scattering) and the physical defaults of the runs.
 COMMON = dict(T_K=300.0, eps_F=0.4, mech_mask=63, alpha=0.1, Nk=240, Lk_hvF=5.0, n_theta=64,
-              pauli_norm=0, final_state=0, max_coll=32, seed=1, stream_id=0)
+              pauli_norm=0, final_state=0, max_coll=32, seed=1, stream_id=0, splitting=0)
 
 
 def _w(**kw):

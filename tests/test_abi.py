@@ -127,3 +127,14 @@ def test_band_minimum_law_fields_are_checked(lib):
     cfg.width_nm.hi = 6.5                      # a deterministic width: no random input
     s = pgc.pgc_query_sizes(cfg)
     assert (s["P"], s["Q"]) == (1, 1)
+
+
+def test_splitting_field_is_checked(lib):
+    cfg = pgc.pgc_config_default()
+    assert cfg.splitting == pgc.PGC_SPLIT_LIE
+    cfg.splitting = 5
+    with pytest.raises(pgc.PgcError) as e:
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EINVAL
+    cfg.splitting = pgc.PGC_SPLIT_STRANG
+    assert pgc.pgc_query_sizes(cfg)["P"] == 1
