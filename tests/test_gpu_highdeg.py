@@ -68,6 +68,27 @@ def test_fp64_trajectories_match_oracle(name, p):
     s.close()
 
 
+def test_observations_at_degree_30_match_oracle():
+    """FP64 degree-30 run: observables and the reconstructed distribution at points off the
+    nodes, in passes of exactly 32 and 64 points, equal the oracle's on the same state."""
+    pgc = _pgc()
+    p = _deg(W.TEST3_WIDTH_1E4, 30, N=900, precision="fp64")
+    s = pgc.Simulation(p, max_outputs=4)
+    s.step(30, 30)
+    o = O.Oracle(p, init_khat=s.state())
+    for nz in (32, 64):
+        z = np.random.default_rng(nz).uniform(-1.0, 1.0, size=(nz, 1))
+        g = s.observe_at(z)
+        r = np.array([o.observe_at(zz) for zz in z])
+        for comp in (0, 2, 3):
+            assert _normwise(g[:, comp], r[:, comp]) <= 1e-12
+    z = np.array([[-0.95], [0.1], [0.77]])
+    Hg, mg = s.reconstruct_f(z)
+    Hr, mr = o.reconstruct_f(z)
+    assert np.abs(Hg.astype(np.int64) - Hr.astype(np.int64)).sum() <= 2 * len(z)
+    s.close()
+
+
 @pytest.mark.parametrize("M", [8, 25])
 def test_fp32_moments_match_oracle(M):
     """Means within 1e-3 normwise.  The variance over z is the small difference of node values

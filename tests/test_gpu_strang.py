@@ -48,7 +48,8 @@ FP64 = [("det", W.scaled(W.DET_FP64_1E4, N=5000, splitting=1), 120),
         ("gap", W.scaled(W.GAP_UQ_1E6, N=3000, precision="fp64", splitting=1), 60),
         ("width", W.scaled(W.TEST2_WIDTH_1E6, N=2000, precision="fp64", splitting=1), 40),
         ("gap_field", W.scaled(W.GAP_FIELD_UQ_4E6, N=500, precision="fp64", splitting=1), 20),
-        ("gap_current_max", W.scaled(W.GAP_UQ_1E6, N=2000, precision="fp64", splitting=1, pauli_norm=1), 40)]
+        ("gap_current_max", W.scaled(W.GAP_UQ_1E6, N=2000, precision="fp64", splitting=1, pauli_norm=1), 40),
+        ("field_M10", W.scaled(W.TEST3_FIELD_1E4, N=1000, M=10, Q1=11, precision="fp64", splitting=1), 40)]
 
 
 @pytest.mark.parametrize("name,p,steps", FP64, ids=[c[0] for c in FP64])
