@@ -561,13 +561,13 @@ def main():
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        host_state = sim.state()
+        host_state = sim.state_native()              # the ensemble in page-locked host memory (device layout)
         sim.close()
         sim2 = pgc.Simulation(p, max_outputs=cap)
         barrier()
         e0 = time.perf_counter()
         for k in range(K):
-            sim2.set_state(host_state)               # H2D of the step's input state (pinned staging)
+            sim2.set_state_native(host_state)        # H2D of the step's input state
             sim2.step(S, every)
             m = sim2.moments()                       # D2H of the moment series (synchronizes)
         barrier()

@@ -212,6 +212,18 @@ pgc_status pgc_observe_at(pgc_ctx *ctx, const double *h_z, int32_t nz, double *h
 pgc_status pgc_get_state(pgc_ctx *ctx, double *h_khat);
 pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat);
 
+/* The state in the device layout and precision (R khat[2][P][ld], the state_bytes of
+ * pgc_query_sizes; under the Strang splitting the stored, half-drift-ahead coefficients, so that
+ * a get/set pair round-trips exactly), copied to or from host memory without conversion: for
+ * checkpoints, and for feeding an ensemble from page-locked host memory at copy speed.
+ * pgc_get_state_native synchronizes.  pgc_set_state_native only queues the copy and the
+ * histogram of the new state (which becomes f^n for the next step, as in pgc_set_state) on the
+ * context stream: from page-locked memory the copy is asynchronous, and h_state must stay valid
+ * and unchanged until the stream has passed it (e.g. until the next synchronizing call).
+ * Errors: PGC_EINVAL for a NULL argument; PGC_ECUDA if the copy fails. */
+pgc_status pgc_get_state_native(pgc_ctx *ctx, void *h_state);
+pgc_status pgc_set_state_native(pgc_ctx *ctx, const void *h_state);
+
 /* Counters PGC_CNT_* (uint64 [PGC_NUM_COUNTERS]); synchronizes. */
 pgc_status pgc_counters(pgc_ctx *ctx, uint64_t *h_counters);
 

@@ -897,6 +897,30 @@ pgc_status pgc_set_state(pgc_ctx *ctx, const double *h_khat)
     return PGC_OK;
 }
 
+pgc_status pgc_get_state_native(pgc_ctx *ctx, void *h_state)
+{
+    if (!ctx || !h_state) return fail(ctx, PGC_EINVAL, "NULL argument");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const size_t bytes = (size_t)2 * ctx->t.P * ctx->b.ld * (ctx->cfg.precision == PGC_FP64 ? 8 : 4);
+    cudaError_t e = cudaMemcpyAsync(h_state, ctx->b.state, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state copy");
+    return PGC_OK;
+}
+
+pgc_status pgc_set_state_native(pgc_ctx *ctx, const void *h_state)
+{
+    if (!ctx || !h_state) return fail(ctx, PGC_EINVAL, "NULL argument");
+    if (ctx->failed) return fail(ctx, PGC_ESTATE, "context failed earlier: " + ctx->err);
+    const size_t bytes = (size_t)2 * ctx->t.P * ctx->b.ld * (ctx->cfg.precision == PGC_FP64 ? 8 : 4);
+    ctx->sampled = false;
+    cudaError_t e = cudaMemcpyAsync(ctx->b.state, h_state, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
+    // the histogram of the uploaded state becomes f^n (the Pauli normaliser is kept)
+    if (ctx->T_out > 0) return observe_current(ctx, false, false);
+    return PGC_OK;
+}
+
 pgc_status pgc_counters(pgc_ctx *ctx, uint64_t *h)
 {
     if (!ctx || !h) return fail(ctx, PGC_EINVAL, "NULL argument");

@@ -73,6 +73,8 @@ SIGNATURES = {
     "pgc_observe_at": (C.c_int, [_vp, _dp, C.c_int32, _dp]),
     "pgc_get_state": (C.c_int, [_vp, _dp]),
     "pgc_set_state": (C.c_int, [_vp, _dp]),
+    "pgc_get_state_native": (C.c_int, [_vp, _vp]),
+    "pgc_set_state_native": (C.c_int, [_vp, _vp]),
     "pgc_counters": (C.c_int, [_vp, _u64p]),
     "pgc_get_hist": (C.c_int, [_vp, _u32p, _u32p]),
     "pgc_profile": (C.c_int, [_vp, C.c_int32]),
@@ -188,6 +190,14 @@ def pgc_get_state(ctx, P: int, N: int):
 def pgc_set_state(ctx, khat):
     a = np.ascontiguousarray(khat, dtype=np.float64)
     _check(lib().pgc_set_state(_vp(ctx), _ptr(a, _dp)), _vp(ctx))
+
+
+def pgc_get_state_native(ctx, h_ptr: int):
+    _check(lib().pgc_get_state_native(_vp(ctx), _vp(h_ptr)), _vp(ctx))
+
+
+def pgc_set_state_native(ctx, h_ptr: int):
+    _check(lib().pgc_set_state_native(_vp(ctx), _vp(h_ptr)), _vp(ctx))
 
 
 def pgc_counters(ctx):
@@ -391,6 +401,23 @@ class Simulation:
 
     def set_state(self, khat):
         pgc_set_state(self.ctx, khat)
+
+    def state_native(self):
+        """The state in the device layout and precision, in a page-locked host tensor (uint8)."""
+        import torch
+
+        n = pgc_query_sizes(self.cfg)["state_bytes"]
+        h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        pgc_get_state_native(self.ctx, h.data_ptr())
+        return h
+
+    def set_state_native(self, h):
+        """Queue the upload of a state_native() tensor (the caller keeps it alive and unchanged
+        until the context stream has passed the copy)."""
+        n = pgc_query_sizes(self.cfg)["state_bytes"]
+        if h.device.type != "cpu" or h.numel() * h.element_size() != n or not h.is_contiguous():
+            raise ValueError("expected a contiguous host tensor of %d bytes" % n)
+        pgc_set_state_native(self.ctx, h.data_ptr())
 
     def counters(self):
         return pgc_counters(self.ctx)

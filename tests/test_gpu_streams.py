@@ -62,3 +62,30 @@ def test_context_created_while_dropped_work_is_queued():
         new.step(15, 0)
         assert np.array_equal(new.state(), ref)
         new.close()
+
+
+@pytest.mark.parametrize("prec,split", [("fp32", 0), ("fp64", 0), ("fp32", 1)])
+def test_native_state_transfer_round_trips(prec, split):
+    """pgc_get_state_native / pgc_set_state_native: a checkpoint of context a at step 15,
+    uploaded into context b at the same step (same key, different history), makes b continue
+    bit-identically to a.  The Pauli normaliser is the current maximum here, so that it does
+    not depend on the history either."""
+    from paper_2404_19602_gb300 import pgc
+
+    p = W.scaled(W.GAP_UQ_1E6, N=20001, precision=prec, splitting=split, pauli_norm=1)
+    a = pgc.Simulation(p, max_outputs=4)
+    b = pgc.Simulation(p, init_khat=0.9 * a.state(), max_outputs=4)
+    a.step(15, 0)
+    b.step(15, 0)
+    assert not np.array_equal(a.state(), b.state())
+    ck = a.state_native()
+    assert ck.is_pinned() and ck.numel() == pgc.pgc_query_sizes(a.cfg)["state_bytes"]
+    b.set_state_native(ck)
+    assert np.array_equal(b.state_native().numpy(), ck.numpy())
+    assert np.array_equal(b.hist()[0], a.hist()[0])
+    a.step(15, 0)
+    b.step(15, 0)
+    assert np.array_equal(a.state(), b.state())
+    assert a.counters()["changed"] > 0
+    a.close()
+    b.close()
