@@ -35,7 +35,8 @@ from paper_2404_19602_gb300 import workloads as W  # noqa: E402
 WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_FIELD_UQ_4E6, "sweep": None,
              "adjoint": W.ADJOINT_1E6,
              "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64"),
-             "sg_error": W.TEST3_WIDTH_1E4, "mc_compare": W.TEST3_WIDTH_1E4}
+             "sg_error": W.TEST3_WIDTH_1E4, "mc_compare": W.TEST3_WIDTH_1E4,
+             "gap_uq_strang": W.scaled(W.GAP_UQ_1E6, splitting=1, name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp32_strang")}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -55,7 +56,7 @@ def parse():
                          "(the gap_uq ensemble in the FP64 mode), sg_error (the stochastic-Galerkin error "
                          "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles), mc_compare "
                          "(Test 4: MC-sG against Algorithm 1 at sampled inputs, 5e4 particles, reference 5e6 "
-                         "particles at degree 30)")
+                         "particles at degree 30), gap_uq_strang (the gap_uq ensemble with the Strang splitting)")
     ap.add_argument("--fd-check", action="store_true",
                     help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
