@@ -63,7 +63,7 @@ pgc_status adj_layout(const pgc_ctx *ctx, int64_t n_steps, int32_t K, AdjLayout 
     L->qcount = take(8 * 4);
     L->counters = take(8 * 8);
     L->part1 = take((size_t)kMaxGrid1 * Q * 3 * 8);
-    L->part2 = take((size_t)kGrid2 * Q * 3 * 8);
+    L->part2 = take((size_t)kGrid2Max * Q * 3 * 8);   // the replay runs the forward phase-2 grid
     L->aqueue = take((size_t)ctx->b.N * 4);
     L->aqcount = take(4 * 4);
     L->grad = take(NTH * 8);

@@ -532,8 +532,8 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     L->off_counters = take(8 * 8);
     L->off_nmax = take((size_t)L->Q * 4);
     L->off_part1 = take((size_t)2 * kMaxGrid1 * L->Q * 3 * 8);
-    L->off_part2 = take((size_t)kGrid2 * L->Q * 3 * 8);
-    L->off_partN = take((size_t)2 * kGrid2 * L->Q * 3 * 8);
+    L->off_part2 = take((size_t)kGrid2Max * L->Q * 3 * 8);
+    L->off_partN = take((size_t)2 * kGrid2Max * L->Q * 3 * 8);
     L->off_marks = take((size_t)kMarkSlots * L->mark_words * 4);
     L->off_tables = take(kTableBytes);
     L->off_series = take((size_t)c->max_outputs * L->rec_len * 8);
@@ -735,7 +735,7 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
         f.t_fs = (n + 1) * ctx->t.dt;
         f.g2 = g2;
         f.g3 = g3;
-        const double *p3 = g3 > 0 ? ctx->b.partN + (n & 1) * (int64_t)kGrid2 * Q3 : nullptr;
+        const double *p3 = g3 > 0 ? ctx->b.partN + (n & 1) * (int64_t)kGrid2Max * Q3 : nullptr;
         k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1 + (n & 1) * ctx->b.part1_stride, ctx->b.part2, p3, f,
                                              ctx->series + ctx->T_out * ctx->rec_len);
         count_launch();

@@ -30,6 +30,10 @@ constexpr int kPhase1Threads = 256;
 constexpr int kPhase2Threads = 128;
 constexpr int kMaxGrid1 = 4096;   // block partials sized for at most this many phase-1 blocks
 constexpr int kGrid2 = 608;       // phase-2 blocks (grid-stride over the queue)
+// The large shapes (P * Q > 64: many nodes per collision chain, ~20 chains per group in sequence)
+// run five phase-2 blocks per SM, one more wave of latency-bound chains in flight.
+template <int P, int Q> struct Phase2Blocks { static constexpr int per_sm = (P * Q > 64) ? 5 : 4; };
+constexpr int kGrid2Max = 5 * 152; // phase-2 partial sums are sized for this many blocks
 // Block-private histogram window of phase 1: kWin x kWin cells per node around the grid centre,
 // 16-bit counts packed two per 32-bit word in shared memory, flushed to the global histogram once
 // per block.  Cells outside the window go straight to the global histogram.
@@ -87,7 +91,7 @@ struct StepArgs {
     uint32_t *tilectr;       // phase-1 tile counter of this step (nullptr: static tile assignment)
     uint32_t *tilectr_next;  // tile counter of the next step (zeroed by phase 1)
     double *part1;           // [gridDim(phase1)][Q*3]
-    double *part2;           // [kGrid2][Q*3]
+    double *part2;           // [kGrid2Max][Q*3]
     unsigned long long *counters;
     uint32_t key0, key1, stream_id, step;
     int32_t out_step;        // 1: accumulate the moments of the post-step state
@@ -102,7 +106,7 @@ struct StepArgs {
     uint32_t *Hnext2;        // f^{n+2}
     uint32_t *queue_next;    // collider queue of step n + 1 (its counter is qcount_next)
     uint32_t *mark_next;     // bitmap of step n + 1
-    double *partN;           // [kGrid2][Q*3] moments of step n + 1 of the particles finished here
+    double *partN;           // [kGrid2Max][Q*3] moments of step n + 1 of the particles finished here
     int32_t out_next;        // 1: step n + 1 is a moment step
     const Nodes<P, Q, R> *nd_dev;  // device copy of nd (phase 2 stages it into shared memory)
 };
@@ -894,7 +898,7 @@ __device__ __forceinline__ void phase2_block(const StepArgs<P, Q, R> &a, int bid
 }
 
 template <int P, int Q, typename R, bool EXT>
-__global__ void __launch_bounds__(kPhase2Threads, 4)
+__global__ void __launch_bounds__(kPhase2Threads, Phase2Blocks<P, Q>::per_sm)
 k_phase2(const __grid_constant__ StepArgs<P, Q, R> a)
 {
     __shared__ R sred[ProjRed<P, Q, R>::value ? (kPhase2Threads / 32) * ProjRed<P, Q, R>::warp_elems : 1];

@@ -98,7 +98,7 @@ public:
         // phase 2: one resident wave (its work is one latency-bound collision chain per group)
         int per_sm2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_phase2<P, Q, R, true>, kPhase2Threads, 0);
-        grid2_ = std::max(1, std::min(kGrid2, num_sms * std::max(per_sm2, 1)));
+        grid2_ = std::max(1, std::min(P * Q > 64 ? kGrid2Max : kGrid2, num_sms * std::max(per_sm2, 1)));
         // the fused step kernel: as many collider groups as grid2_ blocks of phase 2 carry
         grid2f_ = std::max(1, grid2_ * kPhase2Threads / kPhase1Threads);
     }
@@ -159,7 +159,7 @@ public:
         a.mark_clear = M(n + 1);
         a.skip = nullptr;
         a.part1 = b_.part1 + (n & 1) * b_.part1_stride;
-        a.partN = b_.partN ? b_.partN + ((n + 1) & 1) * (int64_t)kGrid2 * Q * 3 : nullptr;
+        a.partN = b_.partN ? b_.partN + ((n + 1) & 1) * (int64_t)kGrid2Max * Q * 3 : nullptr;
         a.step = (uint32_t)n;
         return a;
     }
