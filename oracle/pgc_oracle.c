@@ -17,7 +17,9 @@
  * Parity status of the functions (what pins each one, see tests/test_oracle_*.py):
  *   philox / uniform ........ published Random123 known-answer vectors
  *   li2 ..................... scipy spence, closed values Li2(-1), Li2(1/2)
- *   gauss_legendre / psi .... polynomial exactness, orthonormality, numpy leggauss
+ *   gauss_legendre / psi .... polynomial exactness, orthonormality, numpy leggauss (up to 31
+ *                             nodes and degree 30, the stochastic-Galerkin error study)
+ *   observe_at .............. Galerkin mean/variance vs brute-force z sampling (tiny ensembles)
  *   rates ................... 2-D quadrature of the transition rates S, detailed balance
  *   edge_T / edge angle ..... T(0,c)=2pi, Bessel closed form, KS vs the density
  *   AC / K / OP angles ...... KS vs the CDFs (th +- sin th)/2pi, uniform
