@@ -132,16 +132,17 @@ def _src_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
+def _traffic(kernel: str, workload: str, key: str = "dram_bytes_per_launch"):
+    """A per-launch figure of `kernel` (DRAM bytes, or warp instructions with key
+    "warp_inst_per_launch") from the committed ncu summary, if it was taken on the current kernel
+    sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
         e = d[workload][kernel]
         if e.get("src_sha") != _src_sha():
             return None
-        return e["dram_bytes_per_launch"]
+        return e[key]
     except Exception:
         return None
 
@@ -559,6 +560,18 @@ def main():
                 "phase1_ms": prof["phase1_ms"], "phase2_ms": prof["phase2_ms"],
                 "bytes_per_launch": by, "samples": prof["samples"], "pipelined": fused}
 
+    # the issue roofline of the same kernel: its ncu instruction count per launch over the event
+    # time, against one warp instruction per clock per SM sub-partition at the maximum SM clock
+    issue = None
+    inst = _traffic(dominant, args.workload, "warp_inst_per_launch")
+    if inst and ms_dom > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        ach_i, peak_i = inst / (ms_dom / 1e3), sms * 4 * mhz * 1e6
+        issue = {"bound": "issue", "achieved": ach_i, "peak": peak_i, "unit": "warp-inst/s", "frac": ach_i / peak_i,
+                 "kernel": dominant, "warp_inst_per_launch": inst,
+                 "peak_source": "%d SMs x 4 schedulers x 1 warp instruction per clock x %.0f MHz" % (sms, mhz)}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -597,6 +610,7 @@ def main():
                              "across the time steps of one step when it fits",
                        "parallelism": "independent ensembles per GPU" if world > 1 else "1 GPU"},
             "roofline": roofline,
+            "roofline_issue": issue,
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": launches,
