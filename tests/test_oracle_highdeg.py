@@ -58,3 +58,33 @@ def test_degree_zero_is_the_deterministic_run_at_the_centre():
     d.step(60, 20)
     assert np.array_equal(g.state(), d.state())
     assert np.array_equal(g.moments()["mean"], d.moments()["mean"])
+
+
+def _energy_curve(base, M, steps=40):
+    z, w = np.polynomial.legendre.leggauss(64)
+    o = O.Oracle(W.scaled(base, N=300, M=M, Q1=M + 1, mech_mask=0))
+    o.step(steps, steps)
+    return np.array([o.observe_at([zz])[2] for zz in z]), w / 2.0
+
+
+def test_ballistic_sg_error_is_exact_for_an_affine_field():
+    """Scattering off, uncertain field: every particle's k(z) = k0 - (e/hbar) E(z) t is affine in z,
+    so any degree M >= 1 represents it exactly and the Test 3 error vanishes to rounding."""
+    ref, w = _energy_curve(W.TEST3_FIELD_1E4, 30)
+    for M in (1, 2, 5):
+        e, _ = _energy_curve(W.TEST3_FIELD_1E4, M)
+        assert np.sqrt(((e - ref) ** 2 * w).sum()) < 1e-13
+
+
+def test_ballistic_sg_error_converges_spectrally_for_the_width():
+    """Scattering off, uncertain width: k(z) depends analytically on z through the initial sampling
+    at eps0(z) = pi hbar vF / W(z), so the L2(I_z) error of the energy against degree 30 falls
+    geometrically with M (measured ~50x per two degrees)."""
+    ref, w = _energy_curve(W.TEST3_WIDTH_1E4, 30)
+    err = []
+    for M in (2, 4, 6, 8):
+        e, _ = _energy_curve(W.TEST3_WIDTH_1E4, M)
+        err.append(np.sqrt(((e - ref) ** 2 * w).sum()))
+    assert err[0] > 1e-7
+    for a, b in zip(err, err[1:]):
+        assert b < a / 10.0, err
