@@ -225,3 +225,19 @@ def test_mc_sg_and_mc_mc_estimates_agree():
     tol = 4.0 * np.sqrt(se ** 2 + 1e12 / 200_000)
     assert abs(sg - v.mean()) <= tol, (sg, v.mean(), tol)
     assert abs(sg) > 10 * tol / 4.0          # a drift well resolved at this time
+
+
+def test_ballistic_sg_error_converges_spectrally_fp64():
+    """Scattering off (FP64): the Test 3 error of the energy against degree 30 falls geometrically
+    with M for the uncertain width and vanishes to rounding for the affine field."""
+    from paper_2404_19602_gb300 import sg_error
+
+    w = W.scaled(W.TEST3_WIDTH_1E4, N=2000, mech_mask=0, precision="fp64")
+    e = sg_error.sg_error(w, (2, 4, 6, 8), 30, (40,))
+    errs = [float(e[M][0]) for M in (2, 4, 6, 8)]
+    assert errs[0] > 1e-7
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 10.0, errs
+    f = W.scaled(W.TEST3_FIELD_1E4, N=2000, mech_mask=0, precision="fp64")
+    e = sg_error.sg_error(f, (1, 3), 30, (40,))
+    assert max(float(e[1][0]), float(e[3][0])) < 1e-12, e
