@@ -88,3 +88,15 @@ def test_ballistic_sg_error_converges_spectrally_for_the_width():
     assert err[0] > 1e-7
     for a, b in zip(err, err[1:]):
         assert b < a / 10.0, err
+
+
+@pytest.mark.parametrize("base", ["width", "gap_field"])
+def test_observe_at_the_nodes_gives_the_moment_record(base):
+    """The oracle's two observation routines agree: observables of the particles reconstructed at
+    a quadrature node (Eq. (23) at z_q) are the node values of its moment record."""
+    p = {"width": W.scaled(W.TEST3_WIDTH_1E4, N=700), "gap_field": W.scaled(W.GAP_FIELD_UQ_4E6, N=300)}[base]
+    o = O.Oracle(p)
+    o.step(20, 20)
+    rec = o.moments()["nodes"][-1]
+    for q, zq in enumerate(o.tables()["z"]):
+        assert np.allclose(o.observe_at(zq), rec[q], rtol=1e-12, atol=1e-9)
