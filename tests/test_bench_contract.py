@@ -37,3 +37,20 @@ def test_reference_arm_prints_on_rank_zero_only():
 def test_reference_line_for_another_workload():
     d = json.loads(_run(None, "--workload", "det")[0])
     assert d["config"]["workload"].startswith("det_") and d["value"] > 0
+
+
+def test_traffic_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
+    """The DRAM bytes and instruction counts of profiles/traffic.json are used only while the
+    kernel sources hash to the value they were captured on."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    e = t["gap_uq"]["k_step"]
+    if e["src_sha"] == bench._src_sha():
+        assert bench._traffic("k_step", "gap_uq") == e["dram_bytes_per_launch"]
+        assert bench._traffic("k_step", "gap_uq", "warp_inst_per_launch") == e["warp_inst_per_launch"]
+    monkeypatch.setattr(bench, "_src_sha", lambda: "0" * 16)
+    assert bench._traffic("k_step", "gap_uq") is None
+    assert bench._traffic("no_such_kernel", "gap_uq") is None
+    assert bench.throughput(1000, 2, 10, 5, 11.0) == 1000 * 2 * 10 * 5 / 11e-3
