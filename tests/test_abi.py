@@ -138,3 +138,37 @@ def test_splitting_field_is_checked(lib):
     assert e.value.status == pgc.PGC_EINVAL
     cfg.splitting = pgc.PGC_SPLIT_STRANG
     assert pgc.pgc_query_sizes(cfg)["P"] == 1
+
+
+def test_plain_c_consumer_compiles_links_and_queries(lib, tmp_path):
+    """The header is plain C99 (no C++ constructs), and a C program linked against the library
+    can fill a default configuration and query the buffer sizes without a GPU."""
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "consumer.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "pgc.h"
+int main(void)
+{
+    pgc_config c;
+    size_t s = 0, h = 0, w = 0;
+    int32_t P = 0, Q = 0;
+    pgc_config_default(&c);
+    c.eps0_eV.lo = 0.05; c.eps0_eV.hi = 0.15; c.degree_M = 5; c.quad_per_dim = 6; c.n_particles = 1000;
+    if (pgc_query_sizes(&c, &s, &h, &w, &P, &Q) != PGC_OK) { puts(pgc_last_error(NULL)); return 1; }
+    printf("%d %d %zu\n", P, Q, s);
+    c.splitting = 7;
+    return pgc_query_sizes(&c, &s, &h, &w, &P, &Q) == PGC_EINVAL ? 0 : 2;
+}
+''')
+    exe = tmp_path / "consumer"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I" + os.path.join(ROOT, "include"),
+                           str(src), "-o", str(exe), "-L" + libdir, "-lpgc", "-Wl,-rpath," + libdir])
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.split() == ["6", "6", str(2 * 6 * 1024 * 4)]
