@@ -115,6 +115,7 @@ def lib():
             L.orc_step_particles.argtypes = [vp, i64p, C.c_int64]
             L.orc_set_step.argtypes = [vp, C.c_int64]
             L.orc_set_nmax.argtypes = [vp, u32p]
+            L.orc_set_hist.argtypes = [vp, u32p]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
@@ -350,6 +351,11 @@ class Oracle:
     def set_nmax(self, nmax):
         a = np.ascontiguousarray(nmax, dtype=np.uint32)
         lib().orc_set_nmax(self._h, _u32p(a))
+
+    def set_hist(self, H):
+        """Replace the histogram f^n [Q][Nk][Nk] that the next step's Pauli test reads (test hook)."""
+        a = np.ascontiguousarray(H, dtype=np.uint32).reshape(self.Q, self.Nk, self.Nk)
+        lib().orc_set_hist(self._h, _u32p(a))
 
     def observe_at(self, z):
         z = np.ascontiguousarray(np.atleast_1d(z), dtype=np.float64)

@@ -25,6 +25,14 @@
  *   AC / K / OP angles ...... KS vs the CDFs (th +- sin th)/2pi, uniform
  *   fd sampling, density .... numerical quadrature of eps*FD(eps), T->0 limit
  *   drift ................... closed form k(t) = k(0) - (e/hbar) E t (mechanisms off)
+ *   histogram / Nmax ........ numpy histogram of floor((k + Lk)/dk) of the node values
+ *                             reconstructed with numpy's Legendre basis; its maximum
+ *   Pauli test .............. planted histograms: saturated (every in-grid candidate rejected,
+ *                             the particles only drift), empty (= the run without the test,
+ *                             bit for bit), uniform f (rejected share = f, binomial), the
+ *                             current-maximum normaliser, a half-plane histogram under a strong
+ *                             field (accepted states end left of -(e/hbar) E dt: the look-up
+ *                             moves with the drift, Lie and Strang), zero outside the grid
  *   full step ............... conservation, positivity, zero-field symmetry, stationarity of the
  *                             Maxwellian, collision-count statistics, brute-force z sampling of
  *                             the Galerkin mean/variance, degenerate interval = deterministic run.
@@ -909,7 +917,8 @@ static void step_once(orc_state *S)
 }
 
 /* Test hook: advance only the listed particles by one time step (index S->step) against the
- * current histogram; neither the step counter nor the histogram change. */
+ * current histogram; neither the step counter nor the histogram change.  The event counters
+ * (attempts, real, rejected, capped) are added to. */
 void orc_step_particles(void *st, const int64_t *idx, int64_t n)
 {
     orc_state *S = (orc_state *)st;
@@ -920,6 +929,17 @@ void orc_step_particles(void *st, const int64_t *idx, int64_t n)
     int64_t att = 0, real = 0, rej = 0, cap = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : att, real, rej, cap)
     for (int64_t j = 0; j < n; ++j) step_particle(S, idx[j], S->step, S->H, Nmx, &att, &real, &rej, &cap);
+    S->n_coll_attempts += att;
+    S->n_real += real;
+    S->n_rejected += rej;
+    S->n_capped += cap;
+}
+
+/* Test hook: replace the histogram f^n [Q][Nk][Nk] that the next step's Pauli test reads. */
+void orc_set_hist(void *st, const uint32_t *H)
+{
+    orc_state *S = (orc_state *)st;
+    memcpy(S->H, H, sizeof(uint32_t) * (size_t)S->Q * S->cfg.Nk * S->cfg.Nk);
 }
 
 /* Test hook: set the step counter (the Philox counter word of the next step). */
