@@ -52,7 +52,7 @@ cudaError_t part_address(int dev, void **out)
 extern "C" pgc_status pgc_observe_static(pgc_ctx *ctx, uint32_t *d_hist_out, double *d_record_out, void *stream)
 {
     if (!ctx) return PGC_EINVAL;
-    if (ctx->failed) { ctx->err = "context failed earlier"; return PGC_ESTATE; }
+    if (ctx->failed) { ctx->err = "context failed earlier: " + ctx->err; return PGC_ESTATE; }
     if (!d_hist_out || !d_record_out) { ctx->err = "pgc_observe_static: output pointers must be non-NULL"; return PGC_EINVAL; }
     const int Q = ctx->t.Q, g1 = ctx->run->grid1();
     const size_t need = (size_t)g1 * Q * 3 * sizeof(double);
@@ -76,7 +76,9 @@ extern "C" pgc_status pgc_observe_static(pgc_ctx *ctx, uint32_t *d_hist_out, dou
     if (e == cudaSuccess) e = ctx->run->observe_into(d_hist_out, (double *)part, s);
     if (e == cudaSuccess) e = pgc::launch_finalize(ctx, (const double *)part, g1, ctx->step * ctx->t.dt, d_record_out, s);
     if (e != cudaSuccess) {
+        // as every other entry point: a CUDA error leaves the context failed (PGC_ESTATE after)
         ctx->err = std::string("pgc_observe_static: ") + cudaGetErrorString(e);
+        ctx->failed = true;
         return PGC_ECUDA;
     }
     return PGC_OK;

@@ -29,8 +29,13 @@ def test_static_observation_matches_regular_entry_points():
         H, _ = sim.hist()
         hist = torch.full((Q, Nk, Nk), 7, dtype=torch.int32, device="cuda")
         rec = torch.full((1 + 4 * Q + 8,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         pgc.pgc_observe_static(sim.ctx, hist.data_ptr(), rec.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()
+        if call == 1:
+            # after the first call's one-time set-up, a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
         h = hist.cpu().numpy().view(np.uint32)
         r = rec.cpu().numpy()
         assert np.array_equal(h, H), call
