@@ -512,6 +512,21 @@ __device__ __forceinline__ void phase1_block(const StepArgs<P, Q, R> &a, int bid
     t.skip = a.skip; t.mark = a.mark;
     unsigned int oog = 0u;
     const int64_t tile = (int64_t)blockDim.x * PPT;
+    // A window cell holds 16 bits and a particle adds at most one count to a cell per node, so the
+    // window is flushed to f^{n+1} before the block has counted 65535 particles since the last
+    // flush (block-uniform; with the tile counter a block may take any number of tiles).
+    int64_t since_flush = 0;
+    auto guard_window = [&]() {
+        if (a.use_win && since_flush + tile > 65535) {
+            __syncthreads();
+            flush_window<Q>(swin, a.Hnext, a.ph.Nk, a.win_r0);
+            __syncthreads();
+            for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) swin[j] = 0u;
+            __syncthreads();
+            since_flush = 0;
+        }
+        since_flush += tile;
+    };
     if (a.tilectr) {
         const int64_t ntiles = (a.N + tile - 1) / tile;
         for (;;) {
@@ -520,13 +535,16 @@ __device__ __forceinline__ void phase1_block(const StepArgs<P, Q, R> &a, int bid
             const int64_t tl = s_tile;
             __syncthreads();   // every thread has read s_tile before it is overwritten
             if (tl >= ntiles) break;
+            guard_window();
             phase1_pass<P, Q, R>(a.ph, a.nd, t, tl * tile + (int64_t)threadIdx.x * PPT, swin, a.win_r0,
                                  a.use_win != 0, a.out_step != 0, smom[warp], oog);
         }
     } else {
-        for (int64_t base = (int64_t)bid * tile; base < a.N; base += (int64_t)nb * tile)
+        for (int64_t base = (int64_t)bid * tile; base < a.N; base += (int64_t)nb * tile) {
+            guard_window();
             phase1_pass<P, Q, R>(a.ph, a.nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
                                  a.out_step != 0, smom[warp], oog);
+        }
     }
     oog = warp_sum(oog);
     if (lane == 0 && oog) atomicAdd(&a.counters[4], (unsigned long long)oog);
@@ -557,8 +575,12 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
 // nodes run in parallel, and the projection of Eqs. (28)-(30) and the majorant of Eq. (25) are
 // group reductions by shuffles.
 // ------------------------------------------------------------------------------------------
+#ifndef PGC_GROUP36
+#define PGC_GROUP36 32
+#endif
 template <int Q> struct GroupOf {
-    static constexpr int G = (Q >= 32) ? 32 : (Q > 16 ? 32 : (Q > 8 ? 16 : (Q > 4 ? 8 : (Q > 2 ? 4 : (Q > 1 ? 2 : 1)))));
+    static constexpr int G = (Q == 36) ? PGC_GROUP36
+                           : (Q >= 32) ? 32 : (Q > 16 ? 32 : (Q > 8 ? 16 : (Q > 4 ? 8 : (Q > 2 ? 4 : (Q > 1 ? 2 : 1)))));
     static constexpr int NPL = (Q + G - 1) / G;  // nodes per lane
 };
 

@@ -75,8 +75,8 @@ public:
         init_.key1 = b.key1;
         init_.stream_id = b.stream_id;
         // phase-1 grid: enough resident blocks to fill the GPU, PPT particles per thread; the
-        // shared-memory histogram window needs every cell of a window to receive < 2^16 counts
-        // from one block, and a window that lies inside the grid
+        // shared-memory histogram window lies inside the grid (its 16-bit cells are flushed by
+        // the block before they could overflow, at any N)
         constexpr int PPT = Phase1PPT<P>::value;
         win_bytes_ = (size_t)Q * kWinWords * 4;
         args_.win_r0 = std::max(0, t.Nk / 2 - kWin / 2);
@@ -91,8 +91,6 @@ public:
         per_sm = std::max(per_sm, 1);
         const int64_t need = (b.N + (int64_t)kPhase1Threads * PPT - 1) / ((int64_t)kPhase1Threads * PPT);
         grid1_ = (int)std::max<int64_t>(1, std::min<int64_t>({need, (int64_t)num_sms * per_sm, (int64_t)kMaxGrid1}));
-        const int64_t per_block = (b.N + grid1_ - 1) / grid1_;
-        if (per_block >= 65535) win = false;
         args_.use_win = win ? 1 : 0;
         if (!win) win_bytes_ = 0;
         // phase 2: one resident wave (its work is one latency-bound collision chain per group)
