@@ -2,12 +2,15 @@
 """Throughput of the particle stochastic-Galerkin time step (arXiv:2404.19602) on GB300.
 
 A bench "step" advances the whole ensemble by --time-steps time steps (default 500 of 1 fs);
-the default K = 10 timed steps are one full run of the workload (5000 time steps) from the
-Fermi-Dirac state.  Metric: particle-gPC-steps/s = particles x time steps / device time.
-L2 is flushed (a 256 MiB write) between timed steps; within a step the ensemble state of the
-default workload (48 MB) stays L2-resident across its time steps, as in any run of that size.
+K = 10 timed steps are one full run of the workload (5000 time steps) from the Fermi-Dirac
+state.  Metric: particle-gPC-steps/s = particles x time steps / device time.  The default
+workload is the largest single-GPU one: 4e6 particles, band gap and field random, total degree
+5 (21 coefficients) on 6 x 6 nodes, FP32 state (its 672 MB state exceeds L2; L2 is also flushed
+by a 256 MiB write between timed steps).  The line also carries the error of the moments against
+the FP64 oracle on a reduced ensemble of the same workload (key "parity"), measured outside the
+timed region on the same oracle run that gives the CPU baseline.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload gap_uq|det|gap_field]
+  python bench.py [--gpus N --steps K --warmup W] [--workload gap_field|gap_uq|det|...]
   python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
 Under torchrun (N > 1) each rank advances its own independent ensemble (stream_id = rank):
@@ -49,9 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pgc", choices=["pgc", "reference"])
-    ap.add_argument("--workload", default="gap_uq", choices=sorted(WORKLOADS),
-                    help="gap_uq (1e6 particles, 1 random input), det (1e4, FP64), gap_field (4e6, 2 random "
-                         "inputs), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
+    ap.add_argument("--workload", default="gap_field", choices=sorted(WORKLOADS),
+                    help="gap_field (default: 4e6 particles, 2 random inputs, 21 x 36), gap_uq (1e6 particles, "
+                         "1 random input), det (1e4, FP64), sweep (64 cases in one batched CUDA-graph sequence), adjoint (forward + "
                          "reverse sweep of the steady-current sensitivities, 1e6 particles), gap_uq_fp64 "
                          "(the gap_uq ensemble in the FP64 mode), sg_error (the stochastic-Galerkin error "
                          "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles), mc_compare "
@@ -169,18 +172,28 @@ def throughput(n_particles: int, world: int, time_steps: int, steps: int, ms: fl
     return n_particles * world * time_steps * steps / (ms / 1e3)
 
 
-def cpu_baseline(p):
-    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+def cpu_sample(p):
+    """(particles, time steps) of the bounded oracle sample of a workload: ~2-5 s on 16 cores."""
+    if p["eps0_lo"] == p["eps0_hi"] and p["Ex_lo"] == p["Ex_hi"]:
+        return 10000, 400
+    if p["Q1"] <= 6 and (p["eps0_lo"] == p["eps0_hi"] or p["Ex_lo"] == p["Ex_hi"]):
+        return 20000, 300
+    return 2000, 500
+
+
+def cpu_baseline(p, every):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload.  Returns
+    the baseline record and the oracle's moment series of that sample (for the parity key)."""
     import oracle as O
 
     O.build()
-    n, steps = (20000, 300) if p["M"] and p["Q1"] <= 6 and p["eps0_lo"] != p["eps0_hi"] and p["Ex_lo"] == p["Ex_hi"] else (
-        (10000, 400) if p["eps0_lo"] == p["eps0_hi"] else (2000, 40))
+    n, steps = cpu_sample(p)
     q = W.scaled(p, N=n)
     o = O.Oracle(q)
     t0 = time.perf_counter()
-    o.step(steps, p.get("moments_every", 10))
+    o.step(steps, every)
     dt = time.perf_counter() - t0
+    moments = o.moments()
     cores = O.num_threads()
     # the same oracle on one core, on a tenth of the sample
     n1, s1 = max(n // 10, 200), max(steps // 3, 10)
@@ -188,7 +201,7 @@ def cpu_baseline(p):
     try:
         o1 = O.Oracle(W.scaled(p, N=n1))
         t1 = time.perf_counter()
-        o1.step(s1, p.get("moments_every", 10))
+        o1.step(s1, every)
         dt1 = time.perf_counter() - t1
     finally:
         O.set_threads(0)
@@ -196,7 +209,53 @@ def cpu_baseline(p):
             "sample": "%d particles x %d time steps of the same workload (FP64, OpenMP)" % (n, steps),
             "seconds": round(dt, 3),
             "single_core": {"value": n1 * s1 / dt1, "sample": "%d particles x %d time steps, 1 thread" % (n1, s1),
-                            "seconds": round(dt1, 3)}}
+                            "seconds": round(dt1, 3)}}, (q, steps, moments)
+
+
+def _moment_errors(g, r, n):
+    """Normwise relative errors |a(t) - b(t)| / max_t |b| over the first n output times of the
+    z-mean and z-variance of J_x, V_x and the energy."""
+    import numpy as np
+
+    out = {}
+    for name, comp in (("Jx", 3), ("Vx", 0), ("energy", 2)):
+        for kind in ("mean", "var"):
+            a, b = g[kind][:n, comp], r[kind][:n, comp]
+            scale = float(np.abs(b).max())
+            out["%s_%s" % (kind, name)] = float(np.abs(a - b).max() / scale) if scale > 0 else 0.0
+    return out
+
+
+def parity(pgc, p, q, qsteps, every, ref, timed, S):
+    """Errors of the moment series, outside the timed region.
+
+    fp64_vs_oracle: the library's FP64 mode on the oracle's sample (same workload, particles, seed
+    and time steps) against the FP64 oracle: the same discrete decisions, rounding-level errors.
+    fp32_vs_fp64: the timed run itself (its first S time steps, the whole ensemble) against the
+    FP64 mode on the same ensemble; since the FP64 mode equals the oracle, this is the error of
+    the production path against the FP64 oracle at the full size."""
+    t_samp = q["N"] * qsteps
+    sim = pgc.Simulation(W.scaled(q, precision="fp64"), max_outputs=qsteps // max(every, 1) + 2)
+    sim.step(qsteps, every)
+    g = sim.moments()
+    sim.close()
+    n = min(len(g["t_fs"]), len(ref["t_fs"]))
+    a = _moment_errors(g, ref, n)
+    out = {"fp64_vs_oracle": dict(a, sample="%d particles x %d time steps (%d particle-steps), every %d-th step"
+                                  % (q["N"], qsteps, t_samp, every)), "tolerance": 1e-3}
+    if p.get("precision", "fp32") != "fp64":
+        s64 = pgc.Simulation(W.scaled(p, precision="fp64"), max_outputs=S // max(every, 1) + 2)
+        s64.step(S, every)
+        m64 = s64.moments()
+        s64.close()
+        n = min(len(m64["t_fs"]), len(timed["t_fs"]))
+        b = _moment_errors(timed, m64, n)
+        out["fp32_vs_fp64"] = dict(b, sample="the timed FP32 run, all %d particles, first %d time steps" % (p["N"], S))
+        out.update(b)   # the headline errors: the production path against FP64 at full size
+        out["note"] = ("FP32 rounding now and then flips a cell or threshold decision and the Pauli histogram "
+                       "spreads it: over thousands of steps the FP32 and FP64 trajectories decorrelate and the "
+                       "difference becomes Monte Carlo noise of two equivalent ensembles")
+    return out
 
 
 def run_reference(args):
@@ -534,31 +593,43 @@ def main():
     gpu_ms = sum(a.elapsed_time(b) for a, b in ev)
     prof = pgc.pgc_profile_read(sim.ctx)
     cnt = sim.counters()
+    timed_moments = sim.moments()
     gpu_ms_max = max_over_ranks(gpu_ms, dev)
     N = p["N"]
     value = throughput(N, world, S, K, gpu_ms_max)
 
-    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean launch time.  The
+    # algorithmic bytes of a particle-step are a read and a write of its whole state, 2 x (2 P
+    # esz): 32 B (1 x 1, FP64), 96 B (P = 6), 336 B (P = 21).  The kernels write back only the
+    # coefficients that change (the drifted ones, and the colliders' states), so the bytes they
+    # touch are fewer; both counts are given.
     P, Q = sim.P, sim.Q
     esz = 8 if p.get("precision") == "fp64" else 4
     n_drift = 1 if p["Ex_lo"] == p["Ex_hi"] else 2
     queued = cnt["queued"] / max(cnt["steps"], 1)
-    bytes1 = N * (2 * P * esz + n_drift * esz)          # read the state, write the drifted coefficients
+    unit_bytes = 2 * (2 * P * esz)                       # read + write of one particle's state
+    bytes1 = N * (2 * P * esz + n_drift * esz)          # touched: read the state, write the drifted coefficients
     bytes2 = queued * (2 * (2 * P * esz) + 4)           # colliders: read + write the state, queue index
     peak, peak_kind = _peaks()
     if fused:
         # the fused launch is a whole time step: streaming work of step n + collider work of n - 1
-        dominant, ms_dom, by = "k_step", prof["phase1_ms"], bytes1 + bytes2
+        dominant, ms_dom, by, units = "k_step", prof["phase1_ms"], bytes1 + bytes2, N
     else:
         dominant = "k_phase1" if prof["phase1_ms"] >= prof["phase2_ms"] else "k_phase2"
         ms_dom = max(prof["phase1_ms"], prof["phase2_ms"])
-        by = bytes1 if dominant == "k_phase1" else bytes2
-    achieved = by / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+        by, units = (bytes1, N) if dominant == "k_phase1" else (bytes2, queued)
+    alg = units * unit_bytes
+    achieved = alg / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    touched = by / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _traffic(dominant, args.workload),
                 "kernel": dominant, "peak_source": peak_kind,
+                "bytes_per_unit": unit_bytes, "units_per_launch": units, "bytes_per_launch": alg,
+                "touched_bytes_per_launch": by, "touched_achieved": touched, "touched_frac": touched / peak,
+                "touched_note": "the kernel reads the whole state and writes back only the coefficients the drift "
+                                "changes (and the colliders' states)",
                 "phase1_ms": prof["phase1_ms"], "phase2_ms": prof["phase2_ms"],
-                "bytes_per_launch": by, "samples": prof["samples"], "pipelined": fused}
+                "samples": prof["samples"], "pipelined": fused}
 
     # the issue roofline of the same kernel: its ncu instruction count per launch over the event
     # time, against one warp instruction per clock per SM sub-partition at the maximum SM clock
@@ -593,9 +664,10 @@ def main():
     else:
         sim.close()
 
-    base = None
+    base, par = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(p)
+        base, (q, qsteps, ref) = cpu_baseline(p, every)
+        par = parity(pgc, p, q, qsteps, every, ref, timed_moments, S)
 
     if rank == 0:
         line = {
@@ -607,11 +679,13 @@ def main():
             "config": {"workload": p["name"], "particles_per_gpu": N, "P": P, "Q": Q,
                        "time_steps_per_step": S, "dt_fs": p["dt_fs"], "moments_every": every,
                        "l2": "flushed (256 MiB write) between timed steps; the state stays L2-resident "
-                             "across the time steps of one step when it fits",
+                             "across the time steps of one step when it fits (1e6 x P = 6: 48 MB), and "
+                             "exceeds L2 otherwise (4e6 x P = 21: 672 MB)",
                        "parallelism": "independent ensembles per GPU" if world > 1 else "1 GPU"},
             "roofline": roofline,
             "roofline_issue": issue,
             "cpu_baseline": base,
+            "parity": par,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
