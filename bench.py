@@ -39,7 +39,9 @@ WORKLOADS = {"gap_uq": W.GAP_UQ_1E6, "det": W.DET_FP64_1E4, "gap_field": W.GAP_F
              "adjoint": W.ADJOINT_1E6,
              "gap_uq_fp64": W.scaled(W.GAP_UQ_1E6, precision="fp64", name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp64"),
              "sg_error": W.TEST3_WIDTH_1E4, "mc_compare": W.TEST3_WIDTH_1E4,
-             "gap_uq_strang": W.scaled(W.GAP_UQ_1E6, splitting=1, name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp32_strang")}
+             "gap_uq_strang": W.scaled(W.GAP_UQ_1E6, splitting=1, name="gapU[0.1,0.3]eV_M5_Q6_N1e6_fp32_strang"),
+             "gap_field_tc": W.scaled(W.GAP_FIELD_UQ_4E6, tc_proj=1,
+                                      name="gapU[0.1,0.3]eV_fieldU[1,10]kVcm_M5_Q36_N4e6_fp32_tcgen05_f16x3")}
 METRIC = "particle-gPC-steps/s"
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -59,7 +61,9 @@ def parse():
                          "(the gap_uq ensemble in the FP64 mode), sg_error (the stochastic-Galerkin error "
                          "study of Test 3: degrees 0..25 against 30, two scenarios, 1e4 particles), mc_compare "
                          "(Test 4: MC-sG against Algorithm 1 at sampled inputs, 5e4 particles, reference 5e6 "
-                         "particles at degree 30), gap_uq_strang (the gap_uq ensemble with the Strang splitting)")
+                         "particles at degree 30), gap_uq_strang (the gap_uq ensemble with the Strang splitting), "
+                         "gap_field_tc (the gap_field ensemble with the reconstruction of the streaming kernel on "
+                         "the tensor cores, FP16 hi/lo split)")
     ap.add_argument("--fd-check", action="store_true",
                     help="adjoint workload: also central differences (h = 1e-3 relative, common random numbers)")
     ap.add_argument("--time-steps", type=int, default=500, help="time steps per bench step")
@@ -615,9 +619,10 @@ def main():
         # the fused launch is a whole time step: streaming work of step n + collider work of n - 1
         dominant, ms_dom, by, units = "k_step", prof["phase1_ms"], bytes1 + bytes2, N
     else:
-        dominant = "k_phase1" if prof["phase1_ms"] >= prof["phase2_ms"] else "k_phase2"
+        k1 = "k_phase1_tc" if p.get("tc_proj") else "k_phase1"
+        dominant = k1 if prof["phase1_ms"] >= prof["phase2_ms"] else "k_phase2"
         ms_dom = max(prof["phase1_ms"], prof["phase2_ms"])
-        by, units = (bytes1, N) if dominant == "k_phase1" else (bytes2, queued)
+        by, units = (bytes1, N) if dominant == k1 else (bytes2, queued)
     alg = units * unit_bytes
     achieved = alg / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
     touched = by / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0

@@ -102,6 +102,18 @@ enum { PGC_EPS0_AFFINE = 0, PGC_EPS0_WIDTH = 1 };
  * pgc_get_state / pgc_set_state convert, and the batch and adjoint entry points return
  * PGC_EUNSUPPORTED for it. */
 enum { PGC_SPLIT_LIE = 0, PGC_SPLIT_STRANG = 1 };
+/* Where the streaming kernel reconstructs the node values k(z_q) = sum_h khat_h Psi_h(z_q)
+ * (Eq. (23)), a dense [particles x P] x [P x Q] contraction: OFF, the FP32 FMA pipes (default);
+ * F16X3, the tensor cores (tcgen05, FP32 accumulation) with every FP32 operand split into two
+ * FP16 parts and three products (~22 significant bits, the precision class of the FMA path);
+ * F16, the tensor cores with one FP16 product (FP16 inputs, ~11 bits; node values off by ~1e-3
+ * relative).  Compiled for the FP32 21 x 36 shape (two random inputs, total degree 5); other
+ * shapes return PGC_EUNSUPPORTED.  A context with tc_proj set steps in the two-launch form
+ * (pgc_set_pipeline(ctx, 1) returns PGC_EUNSUPPORTED), and the batch and adjoint entry points
+ * refuse it (their kernels reconstruct on the FMA pipes).  Collisions (phase 2) always
+ * reconstruct on the FMA pipes.  Bit 0 of PGC_CNT_ERROR is set if a wait for the tensor cores
+ * gave up (the step's results are then not valid). */
+enum { PGC_TC_OFF = 0, PGC_TC_F16X3 = 1, PGC_TC_F16 = 2 };
 
 /* counters returned by pgc_counters */
 enum {
@@ -111,7 +123,7 @@ enum {
     PGC_CNT_CAPPED = 3,       /* particle-steps that hit max_collisions */
     PGC_CNT_OUT_OF_GRID = 4,  /* node values outside [-Lk,Lk]^2 in the last histogram */
     PGC_CNT_QUEUED = 5,       /* particle-steps sent to the collider kernel */
-    PGC_CNT_ERROR = 6,        /* device error flag (0 = none) */
+    PGC_CNT_ERROR = 6,        /* device error flags (0 = none; bit 0: a tensor-core wait gave up) */
     PGC_CNT_STEPS = 7,        /* time steps done */
     PGC_NUM_COUNTERS = 8
 };
@@ -142,6 +154,7 @@ typedef struct {
     int32_t eps0_law;        /* PGC_EPS0_AFFINE (default) or PGC_EPS0_WIDTH */
     pgc_interval width_nm;   /* ribbon width, nm (WIDTH law; lo > 0) */
     int32_t splitting;       /* PGC_SPLIT_LIE (default) or PGC_SPLIT_STRANG */
+    int32_t tc_proj;         /* PGC_TC_OFF (default), PGC_TC_F16X3 or PGC_TC_F16 */
 } pgc_config;
 
 typedef struct pgc_ctx pgc_ctx;
@@ -183,7 +196,9 @@ pgc_status pgc_set_pipeline(pgc_ctx *ctx, int32_t on);
 
 /* Copy the recorded time series to the host (synchronizes).  Any pointer may be NULL.
  * h_t_fs[T]; h_mean[T][4], h_var[T][4] with columns (V_x m/s, V_y m/s, energy eV, J_x A/m);
- * h_nodes[T][Q][4] per-node values.  *T_out = number of records (t = 0 included). */
+ * h_nodes[T][Q][4] per-node values.  *T_out = number of records (t = 0 included).
+ * Returns PGC_ETIMEOUT (the series is not copied) if bit 0 of the device error counter is set:
+ * a bounded wait for the tensor cores (tc_proj) gave up in some step. */
 pgc_status pgc_moments(pgc_ctx *ctx, double *h_t_fs, double *h_mean, double *h_var,
                        double *h_nodes, int64_t *T_out);
 
@@ -290,7 +305,10 @@ pgc_status pgc_batch_query_sizes(pgc_ctx *const *ctxs, int32_t n_cases, size_t *
 
 /* Create a batch over ctxs[0..n_cases) (the contexts must outlive it) with caller scratch of the
  * queried size (256-byte aligned).  tile_particles: particles per tile of the phase-1 work list
- * (a multiple of the block pass, 1024 for P <= 8 and 256 otherwise; 0 = 8 passes). */
+ * (a multiple of the block pass, 1024 for P <= 8 and 256 otherwise); 0 = the launch
+ * configuration pgc_batch_autotune chose earlier in this process for a batch of the same basis,
+ * precision and total particle count (within a factor 2), else 8 passes with the default
+ * launch configuration. */
 pgc_status pgc_batch_create(pgc_ctx *const *ctxs, int32_t n_cases, void *d_scratch, int32_t tile_particles,
                             pgc_batch **out);
 
@@ -298,10 +316,20 @@ pgc_status pgc_batch_create(pgc_ctx *const *ctxs, int32_t n_cases, void *d_scrat
  * graph of 10 time steps (the stream must not be the legacy default stream). */
 pgc_status pgc_batch_step(pgc_batch *b, int64_t n_steps, int32_t moments_every, int32_t use_graph);
 
-/* Autotuner: time steps_per_candidate time steps (no moments) for every tile size from one pass
- * to 32768 particles, keep the fastest; *chosen_tile and *ms_per_step (either may be NULL)
- * report it.  The timed steps advance the simulation (tile sizes do not change trajectories). */
+/* Autotuner of the batch's launch configuration: the tile size (from the minimum tile to 32768
+ * particles), the threads per streaming block (128, 256), the particles per thread of the
+ * streaming kernel (4, 2, 1 for the small bases; 1 for P = 21), the streaming blocks per SM
+ * (1 .. resident) and the collider blocks per SM (2 .. resident), by coordinate descent from the
+ * current configuration, two rounds, each candidate timed over steps_per_candidate time steps
+ * (no moments) with CUDA events.  The fastest is applied and cached for later batches of the
+ * same kind (pgc_batch_create with tile_particles = 0); *chosen_tile and *ms_per_step (either
+ * may be NULL) report it.  The timed steps advance the simulation (no launch configuration
+ * changes a trajectory; only the grouping of the FP32 warp sums of the moments differs). */
 pgc_status pgc_batch_autotune(pgc_batch *b, int32_t steps_per_candidate, int32_t *chosen_tile, double *ms_per_step);
+
+/* The batch's launch configuration: cfg5 = {tile, threads per streaming block, particles per
+ * thread, streaming blocks per SM, collider blocks per SM}. */
+pgc_status pgc_batch_launch_config(const pgc_batch *b, int32_t *cfg5);
 
 void pgc_batch_destroy(pgc_batch *b);
 const char *pgc_batch_last_error(const pgc_batch *b);
@@ -327,6 +355,13 @@ const char *pgc_batch_last_error(const pgc_batch *b);
 pgc_status pgc_adjoint_query_sizes(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, size_t *work_bytes);
 pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_t moments_every, int64_t window_steps,
                        const double *h_weights, void *d_work, double *h_value, double *h_grad);
+
+/* The objective of pgc_adjoint without the gradient: advances the context by n_steps as
+ * pgc_step (moments every moments_every steps) and writes h_value = (Jbar, Vbar) over the records
+ * of those steps in (n_steps - window_steps, n_steps] (synchronizes).  Any starting step; no work
+ * memory. */
+pgc_status pgc_window_objective(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every, int64_t window_steps,
+                                double *h_value);
 
 /* Number of kernel launches issued by the library since load (for launch accounting). */
 uint64_t pgc_launch_count(void);

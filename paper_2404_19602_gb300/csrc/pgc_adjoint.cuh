@@ -290,9 +290,10 @@ __device__ void fs_jacobian(const Phys<R> &ph, int l, R kx, R ky, EventAngles<R>
 }
 
 // Replays the collision loop of collide_particle for particle i (same operations, same group
-// layout) for at most `stop` events; on return cx/cy/kx/ky hold the state before event `stop`
-// (or the final state), and *nev the number of events the loop would run.  If `jac` is set, the
-// mechanism of every node at event `stop` is returned in l_out[] (6 = unchanged).
+// layout; an event that changes no node leaves the coefficients, rates and majorant untouched)
+// for at most `stop` events; on return cx/cy/kx/ky hold the state before event `stop` (or the
+// final state), and *nev the number of events the loop would run.  The mechanism of every node
+// at event `stop` is returned in l_out[] (6 = unchanged).
 template <int P, int Q, typename R>
 __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const AdjArgs<P, Q, R> &a,
                                               int64_t i, int r, unsigned gmask, int stop, R cx[P], R cy[P],
@@ -367,6 +368,7 @@ __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, 
         EventAngles<R> ang;
         ang.reset(u01<R>(rr.w));
         const R target = u01<R>(rr.y) * Gt;
+        bool changed = false;
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
@@ -388,15 +390,17 @@ __device__ __forceinline__ void replay_events(const Phys<R> &ph, const Nodes<P, 
                 const int cl = cell_of(ph, nd.lkx[q], nkx + nd.dq[q], nky);
                 if (cl >= 0) accept = pauli_accept(a.Hn[(int64_t)q * NN + cl], a.nmax[q], rr.z);
             }
-            if (accept) { kx[s] = nkx; ky[s] = nky; }
+            if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
         }
-        project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, red);   // the forward's projection
+        if (group_any<G>(changed, gmask)) {   // the forward's projection, reconstruction and majorant
+            project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, red);
 #pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int q = r + s * G;
-            if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+            }
+            Gt = majorant();
         }
-        Gt = majorant();
         tc += dtc;
         ++c;
         ++e;
@@ -441,6 +445,10 @@ k_adj_collide(const __grid_constant__ AdjArgs<P, Q, R> a)
         for (int e = nev - 1; e >= 0; --e) {
             int dummy;
             replay_events(ph, nd, a, i, r, gmask, e, cx, cy, kx, ky, &dummy, lsel, &rr, sred);
+            bool any = false;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) any |= lsel[s] < 6;
+            if (!group_any<G>(any, gmask)) continue;   // an event that changed no node is the identity
             EventAngles<R> ang;
             ang.reset(u01<R>(rr.w));
             // lambda_e = sum_q Psi_q^T J_q^T (W_q^T lambda_{e+1})

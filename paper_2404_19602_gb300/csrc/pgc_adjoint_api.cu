@@ -95,6 +95,49 @@ pgc_status pgc_adjoint_query_sizes(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_e
     return PGC_OK;
 }
 
+// (Jbar, Vbar): averages over the moment records T0.. of the context whose step n (counted from
+// step cur0) lies in (n_steps - window_steps, n_steps] of the z-mean and z-variance of J_x; nout
+// receives the number of such records.
+static cudaError_t window_values(pgc_ctx *ctx, int64_t T0, int64_t cur0, int64_t n_steps, int64_t window_steps,
+                                 std::vector<double> *rec, double value[2], int64_t *nout)
+{
+    const int RL = ctx->rec_len, Q = ctx->t.Q;
+    rec->assign((size_t)(ctx->T_out - T0) * RL, 0.0);
+    cudaError_t e = cudaSuccess;
+    if (!rec->empty()) e = cudaMemcpyAsync(rec->data(), ctx->series + T0 * RL, rec->size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return e;
+    double accJ = 0.0, accV = 0.0;
+    *nout = 0;
+    for (size_t r = 0; r < rec->size() / RL; ++r) {
+        const double *R_ = &(*rec)[r * RL];
+        const int64_t n = (int64_t)llround(R_[0] / ctx->t.dt) - cur0;
+        if (!(n > n_steps - window_steps && n <= n_steps)) continue;
+        accJ += R_[1 + Q * 4 + 3];
+        accV += R_[1 + Q * 4 + 4 + 3];
+        ++*nout;
+    }
+    if (*nout > 0) { value[0] = accJ / *nout; value[1] = accV / *nout; }
+    return cudaSuccess;
+}
+
+pgc_status pgc_window_objective(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every, int64_t window_steps, double *h_value)
+{
+    if (!ctx) return PGC_EINVAL;
+    if (ctx->failed) return afail(ctx, PGC_ESTATE, "context failed earlier");
+    if (!h_value || n_steps < 1 || moments_every < 1 || window_steps < 1 || window_steps > n_steps)
+        return afail(ctx, PGC_EINVAL, "need h_value, n_steps >= 1, moments_every >= 1 and 1 <= window_steps <= n_steps");
+    const int64_t T0 = ctx->T_out, cur0 = ctx->step;
+    pgc_status st = pgc_step(ctx, n_steps, moments_every);
+    if (st != PGC_OK) return st;
+    std::vector<double> rec;
+    int64_t nout = 0;
+    cudaError_t e = window_values(ctx, T0, cur0, n_steps, window_steps, &rec, h_value, &nout);
+    if (e != cudaSuccess) return afail(ctx, PGC_ECUDA, std::string("moments: ") + cudaGetErrorString(e));
+    if (nout == 0) return afail(ctx, PGC_EINVAL, "no moment output inside the window");
+    return PGC_OK;
+}
+
 pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_t moments_every, int64_t window_steps,
                        const double *h_weights, void *d_work, double *h_value, double *h_grad)
 {
@@ -108,6 +151,8 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
         return afail(ctx, PGC_EUNSUPPORTED, "the adjoint differentiates the affine band-minimum endpoints (PGC_EPS0_AFFINE)");
     if (ctx->cfg.splitting != PGC_SPLIT_LIE)
         return afail(ctx, PGC_EUNSUPPORTED, "the adjoint differentiates the Lie splitting (PGC_SPLIT_LIE)");
+    if (ctx->cfg.tc_proj != PGC_TC_OFF)
+        return afail(ctx, PGC_EUNSUPPORTED, "the adjoint replays the FMA reconstruction of the streaming kernel (tc_proj must be PGC_TC_OFF)");
     if (ctx->t.final_state != PGC_FS_PAPER || ctx->t.pauli_mode == PGC_PAULI_CURRENT_MAX)
         return afail(ctx, PGC_EUNSUPPORTED, "the adjoint supports the paper's final states and the initial-maximum or off Pauli modes");
     if (moments_every < 1 || window_steps < 1 || window_steps > n_steps) return afail(ctx, PGC_EINVAL, "need moments_every >= 1 and 1 <= window_steps <= n_steps");
@@ -136,34 +181,25 @@ pgc_status pgc_adjoint(pgc_ctx *ctx, int64_t n_steps, int32_t ckpt_every, int32_
     }
     // ---- objective from the recorded moments ----
     const int RL = ctx->rec_len;
-    std::vector<double> rec((size_t)(ctx->T_out - T0) * RL);
-    if (!rec.empty()) e = cudaMemcpyAsync(rec.data(), ctx->series + T0 * RL, rec.size() * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return afail(ctx, PGC_ECUDA, std::string("moments: ") + cudaGetErrorString(e));
-    std::vector<std::vector<double>> dLdJ(n_steps + 1);
-    double accJ = 0.0, accV = 0.0;
+    std::vector<double> rec;
+    double value[2] = {0.0, 0.0};
     int64_t nout = 0;
-    for (size_t r = 0; r < rec.size() / RL; ++r) {
-        const double *R_ = &rec[r * RL];
-        const int64_t n = (int64_t)llround(R_[0] / ctx->t.dt) - cur0;
-        if (!(n > n_steps - window_steps && n <= n_steps)) continue;
-        ++nout;
-    }
+    e = window_values(ctx, T0, cur0, n_steps, window_steps, &rec, value, &nout);
+    if (e != cudaSuccess) return afail(ctx, PGC_ECUDA, std::string("moments: ") + cudaGetErrorString(e));
     if (nout == 0) return afail(ctx, PGC_EINVAL, "no moment output inside the window");
+    std::vector<std::vector<double>> dLdJ(n_steps + 1);
     for (size_t r = 0; r < rec.size() / RL; ++r) {
         const double *R_ = &rec[r * RL];
         const int64_t n = (int64_t)llround(R_[0] / ctx->t.dt) - cur0;
         if (!(n > n_steps - window_steps && n <= n_steps)) continue;
-        const double mean = R_[1 + Q * 4 + 3], var = R_[1 + Q * 4 + 4 + 3];
-        accJ += mean;
-        accV += var;
+        const double mean = R_[1 + Q * 4 + 3];
         dLdJ[n].assign(Q, 0.0);
         for (int q = 0; q < Q; ++q) {
             const double Jq = R_[1 + q * 4 + 3], wq = ctx->t.w[q];
             dLdJ[n][q] = (h_weights[0] * wq + h_weights[1] * 2.0 * wq * (Jq - mean)) / (double)nout;
         }
     }
-    if (h_value) { h_value[0] = accJ / nout; h_value[1] = accV / nout; }
+    if (h_value) { h_value[0] = value[0]; h_value[1] = value[1]; }
 
     // ---- reverse sweep ----
     DevBuffers rb = ctx->b;  // the replay runs the forward kernels on the work buffers

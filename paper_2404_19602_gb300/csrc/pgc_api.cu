@@ -509,11 +509,17 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     if (c->n_theta_edge < 4 || c->n_theta_edge > kMaxTheta || (c->n_theta_edge & 1)) return bad("n_theta_edge must be even in [4, 256]");
     if (c->max_collisions < 1 || c->max_collisions > 65535) return bad("max_collisions must be in [1, 65535]");
     if (c->max_outputs < 1) return bad("max_outputs must be >= 1");
+    if (c->tc_proj != PGC_TC_OFF && c->tc_proj != PGC_TC_F16X3 && c->tc_proj != PGC_TC_F16)
+        return bad("tc_proj must be PGC_TC_OFF, PGC_TC_F16X3 or PGC_TC_F16");
     L->d = dims_of(*c, &L->P, &L->Q);
     if (L->d > 0 && c->quad_per_dim < c->degree_M + 1) return bad("quad_per_dim must be >= degree_M + 1 (exact projection)");
     if (!shape_compiled(L->d, L->P, L->Q)) {
         *msg = "compiled (P,Q) shapes are (1,1), (6,6), (21,36) and, with one random input, (M+1,M+1) for "
                "M = 1, 2, 3, 4, 6, 8, 10, 12, 15, 20, 25, 30; got (" + std::to_string(L->P) + "," + std::to_string(L->Q) + ")";
+        return PGC_EUNSUPPORTED;
+    }
+    if (c->tc_proj != PGC_TC_OFF && !(L->P == 21 && L->Q == 36 && c->precision == PGC_FP32)) {
+        *msg = "tc_proj (the tensor-core reconstruction) is compiled for the FP32 21 x 36 shape only";
         return PGC_EUNSUPPORTED;
     }
     const int64_t N = c->n_particles;
@@ -679,6 +685,13 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     // collider work is itself throughput-bound (many chains per lane group) and, fused, holds
     // most resident blocks for the whole launch: measured slower, so off by default there
     ctx->pipeline = (ctx->run->fused() && L.P * L.Q <= 64) ? 1 : 0;
+    if (cfg->tc_proj != PGC_TC_OFF) {
+        if ((e = ctx->run->set_tc(cfg->tc_proj)) != cudaSuccess) {
+            delete ctx->run; delete ctx;
+            return fail(nullptr, PGC_EUNSUPPORTED, std::string("tensor-core streaming kernel unavailable: ") + cudaGetErrorString(e));
+        }
+        ctx->pipeline = 0;
+    }
 
     cudaStream_t s = ctx->stream;
     if ((e = cudaMemsetAsync(d_scratch, 0, L.scratch, s)) != cudaSuccess ||
@@ -819,10 +832,14 @@ pgc_status pgc_moments(pgc_ctx *ctx, double *h_t_fs, double *h_mean, double *h_v
     const int64_t T = ctx->T_out;
     const int Q = ctx->t.Q, RL = ctx->rec_len;
     std::vector<double> buf((size_t)T * RL);
+    unsigned long long dev_err = 0;
     cudaError_t e = cudaSuccess;
     if (T > 0) e = cudaMemcpyAsync(buf.data(), ctx->series, buf.size() * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&dev_err, ctx->b.counters + PGC_CNT_ERROR, sizeof(dev_err), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "moments copy");
+    if (dev_err & 1ull) return fail(ctx, PGC_ETIMEOUT, "a bounded wait for the tensor cores gave up in a step; the results are not valid");
     for (int64_t t = 0; t < T; ++t) {
         const double *r = &buf[(size_t)t * RL];
         if (h_t_fs) h_t_fs[t] = r[0];

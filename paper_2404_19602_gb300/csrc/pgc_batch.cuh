@@ -69,11 +69,15 @@ __device__ __forceinline__ int find_case(const int64_t *prefix, int n, int64_t x
     return lo;
 }
 
-template <int P, int Q, typename R>
+// Particles per thread of the batched streaming kernel: the autotuner's choices for a shape
+// (four, two or one for the small bases; one for P = 21).
+template <int P> struct BatchPPTs { static constexpr int n = (P <= 8) ? 3 : 1; static constexpr int v[3] = {Phase1PPT<P>::value, 2, 1}; };
+
+// Any block size up to kPhase1Threads that is a multiple of 32 (the autotuner uses 128 and 256).
+template <int P, int Q, typename R, int PPT>
 __global__ void __launch_bounds__(kPhase1Threads)
 k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
 {
-    constexpr int PPT = Phase1PPT<P>::value;
     constexpr int NW = kPhase1Threads / 32;
     __shared__ double smom[NW][Q * 3];
     __shared__ int64_t stile[kBatchMaxCases + 1];
@@ -123,15 +127,14 @@ k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
         const int64_t p0 = (tile - cd.tile0) * a.tile;
         const int64_t p1 = min(cd.N, p0 + a.tile);
         for (int64_t base = p0; base < p1; base += (int64_t)blockDim.x * PPT)
-            phase1_pass<P, Q, R>(a.ph, nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
-                                 out, smom[warp], oog);
+            phase1_pass<P, Q, R, PPT>(a.ph, nd, t, base + (int64_t)threadIdx.x * PPT, swin, a.win_r0, a.use_win != 0,
+                                      out, smom[warp], oog);
         __syncthreads();
         if (a.use_win) flush_window<Q>(swin, t.Hnext, a.ph.Nk, a.win_r0);
         if (out)
             for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
                 double s = 0.0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) s += smom[w][j];
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += smom[w][j];   // fixed order
                 a.part_tiles[tile * (Q * 3) + j] = s;
             }
         oog = warp_sum(oog);
@@ -269,6 +272,13 @@ struct BatchScratch {
     int64_t max_tiles = 0;
 };
 
+// Launch configuration of a batch: particles per tile, threads per streaming block, particles
+// per thread, streaming and collider blocks per SM.  None of it changes a trajectory (only the
+// grouping of the FP32 warp sums of the moments).
+struct BatchLaunch {
+    int tile = 0, block = kPhase1Threads, ppt = 1, g1_per_sm = 1, g2_per_sm = 4;
+};
+
 class BatchRunner {
 public:
     virtual ~BatchRunner() {}
@@ -276,6 +286,14 @@ public:
     virtual cudaError_t set_tile(int tile, cudaStream_t s) = 0;
     virtual int tile() const = 0;
     virtual int pass() const = 0;
+    // block size, particles per thread and the two grids (not the tile: call set_tile after);
+    // cudaErrorInvalidValue for a configuration this shape cannot run
+    virtual cudaError_t set_launch(int block, int ppt, int g1_per_sm, int g2_per_sm) = 0;
+    virtual BatchLaunch launch() const = 0;
+    // the choices: particles per thread, and the most blocks per SM of each kernel
+    virtual std::vector<int> ppts() const = 0;
+    virtual int max_g1(int block, int ppt) const = 0;
+    virtual int max_g2() const = 0;
     virtual void set_moments_every(int every) = 0;
     // one time step: phase 1, phase 2, finalize (3 launches, step index on the device)
     virtual cudaError_t step(cudaStream_t s) = 0;
@@ -306,11 +324,12 @@ public:
         a_.rec_len = 1 + 4 * Q + 8;
         a_.vF_ms = t0.vF_ms;
         win_bytes_ = a_.use_win ? (size_t)Q * kWinWords * 4 : 0;
-        if (win_bytes_)
-            cudaFuncSetAttribute(k_phase1_batch<P, Q, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase1_batch<P, Q, R>, kPhase1Threads, win_bytes_);
-        grid1_ = std::max(1, num_sms * std::max(per_sm, 1));
+        num_sms_ = num_sms;
+        for (int j = 0; j < BatchPPTs<P>::n; ++j)
+            if (win_bytes_) cudaFuncSetAttribute(kernel1(BatchPPTs<P>::v[j]), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_bytes_);
+        // defaults: 256 threads, the shape's particles per thread, all resident streaming blocks,
+        // four collider blocks per SM
+        set_launch(kPhase1Threads, Phase1PPT<P>::value, max_g1(kPhase1Threads, Phase1PPT<P>::value), 4);
         host_.resize(cases.size());
         for (size_t c = 0; c < cases.size(); ++c) {
             RunnerT<P, Q, R> rc(*cases[c].t, cases[c].b, num_sms);
@@ -332,8 +351,42 @@ public:
         }
     }
 
-    int pass() const override { return kPhase1Threads * Phase1PPT<P>::value; }
+    int pass() const override { return lc_.block * lc_.ppt; }
     int tile() const override { return a_.tile; }
+    BatchLaunch launch() const override { BatchLaunch l = lc_; l.tile = a_.tile; return l; }
+    std::vector<int> ppts() const override { return std::vector<int>(BatchPPTs<P>::v, BatchPPTs<P>::v + BatchPPTs<P>::n); }
+
+    int max_g1(int block, int ppt) const override
+    {
+        const void *k = kernel1(ppt);
+        int per_sm = 0;
+        if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, win_bytes_) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return per_sm;
+    }
+    int max_g2() const override
+    {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase2_batch<P, Q, R>, kPhase2Threads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return per_sm;
+    }
+
+    cudaError_t set_launch(int block, int ppt, int g1_per_sm, int g2_per_sm) override
+    {
+        if ((block != 128 && block != 256) || !kernel1(ppt)) return cudaErrorInvalidValue;
+        if (g1_per_sm < 1 || g1_per_sm > max_g1(block, ppt) || g2_per_sm < 1 || g2_per_sm > max_g2())
+            return cudaErrorInvalidValue;
+        lc_.block = block;
+        lc_.ppt = ppt;
+        lc_.g1_per_sm = g1_per_sm;
+        lc_.g2_per_sm = g2_per_sm;
+        return cudaSuccess;
+    }
     void set_moments_every(int every) override { a_.moments_every = every; }
 
     cudaError_t set_tile(int tile, cudaStream_t s) override
@@ -364,20 +417,37 @@ public:
 
     cudaError_t step(cudaStream_t s) override
     {
-        k_phase1_batch<P, Q, R><<<grid1_, kPhase1Threads, win_bytes_, s>>>(a_);
-        k_phase2_batch<P, Q, R><<<kGrid2, kPhase2Threads, 0, s>>>(a_);
+        const int g1 = num_sms_ * lc_.g1_per_sm, g2 = num_sms_ * lc_.g2_per_sm;
+        switch (lc_.ppt) {
+        case 4: if constexpr (BatchPPTs<P>::n == 3) k_phase1_batch<P, Q, R, 4><<<g1, lc_.block, win_bytes_, s>>>(a_); break;
+        case 2: if constexpr (BatchPPTs<P>::n == 3) k_phase1_batch<P, Q, R, 2><<<g1, lc_.block, win_bytes_, s>>>(a_); break;
+        default: k_phase1_batch<P, Q, R, 1><<<g1, lc_.block, win_bytes_, s>>>(a_); break;
+        }
+        k_phase2_batch<P, Q, R><<<g2, kPhase2Threads, 0, s>>>(a_);
         k_finalize_batch<P, Q, R><<<a_.ncases, 256, 0, s>>>(a_);
         count_launch(3);
         return cudaGetLastError();
     }
 
 private:
+    // the streaming kernel for ppt particles per thread (nullptr if not compiled for this shape)
+    static const void *kernel1(int ppt)
+    {
+        if constexpr (BatchPPTs<P>::n == 3) {
+            if (ppt == 4) return (const void *)k_phase1_batch<P, Q, R, 4>;
+            if (ppt == 2) return (const void *)k_phase1_batch<P, Q, R, 2>;
+        }
+        if (ppt == 1) return (const void *)k_phase1_batch<P, Q, R, 1>;
+        return nullptr;
+    }
+
     std::vector<BatchCase> cases_;
     BatchScratch sc_;
     BatchArgs<P, Q, R> a_{};
     std::vector<CaseDev<P, Q, R>> host_;
     size_t win_bytes_ = 0;
-    int grid1_ = 1;
+    int num_sms_ = 1;
+    BatchLaunch lc_;
 };
 
 template <int P, int Q>

@@ -2,7 +2,10 @@
 // together by one persistent launch sequence per time step, optionally replayed from a CUDA graph,
 // with the tile size chosen by timing candidate tiles on the running simulation.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -54,6 +57,20 @@ struct pgc_batch {
 
 static thread_local std::string g_batch_err;
 
+// Launch configurations chosen by pgc_batch_autotune, per (P, Q, precision, floor(log2(total
+// particles))): a batch created later with tile_particles = 0 starts from the cached choice.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, BatchLaunch> g_tune_cache;
+
+static std::tuple<int, int, int, int> tune_key(const std::vector<pgc_ctx *> &ctxs)
+{
+    int64_t n = 0;
+    for (const pgc_ctx *c : ctxs) n += c->b.N;
+    int bucket = 0;
+    while ((int64_t)1 << (bucket + 1) <= n) ++bucket;
+    return std::make_tuple(ctxs[0]->t.P, ctxs[0]->t.Q, ctxs[0]->cfg.precision, bucket);
+}
+
 namespace {
 
 struct BatchLayout {
@@ -87,6 +104,7 @@ pgc_status check_batch(pgc_ctx *const *ctxs, int32_t n, BatchLayout *L, std::str
         }
         if (c->step != c0->step) { *msg = "all contexts must be at the same step"; return PGC_EINVAL; }
         if (a.splitting != PGC_SPLIT_LIE) { *msg = "the batched kernels run the Lie splitting (PGC_SPLIT_LIE)"; return PGC_EUNSUPPORTED; }
+        if (a.tc_proj != PGC_TC_OFF) { *msg = "the batched kernels reconstruct on the FMA pipes (tc_proj must be PGC_TC_OFF)"; return PGC_EUNSUPPORTED; }
         if (c->stream != c0->stream) { *msg = "all contexts must use the same stream"; return PGC_EINVAL; }
         ntot += c->b.N;
         tiles += (c->b.N + pass - 1) / pass;
@@ -165,8 +183,21 @@ pgc_status pgc_batch_create(pgc_ctx *const *ctxs, int32_t n_cases, void *d_scrat
     }
     b->run = make_batch_runner(c0->t.P, c0->t.Q, c0->cfg.precision, cases, b->sc, sms);
     if (!b->run) { delete b; g_batch_err = "no batch kernel for this shape"; return PGC_EUNSUPPORTED; }
+    int tile = tile_particles;
+    if (tile_particles == 0) {   // the cached autotuner choice for this kind of batch, if any
+        BatchLaunch lc;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(tune_key(b->ctxs));
+            if (it != g_tune_cache.end()) { lc = it->second; have = true; }
+        }
+        if (have && b->run->set_launch(lc.block, lc.ppt, lc.g1_per_sm, lc.g2_per_sm) == cudaSuccess && lc.tile % b->run->pass() == 0)
+            tile = lc.tile;
+        else
+            tile = 8 * b->run->pass();
+    }
     const int pass = b->run->pass();
-    int tile = tile_particles > 0 ? tile_particles : 8 * pass;
     if (tile % pass || tile > 65535) { delete b->run; delete b; g_batch_err = "tile must be a multiple of " + std::to_string(pass) + " and < 65536"; return PGC_EINVAL; }
     const int64_t step0 = c0->step;
     e = cudaMemsetAsync(d_scratch, 0, L.total, b->stream);
@@ -243,42 +274,83 @@ pgc_status pgc_batch_step(pgc_batch *b, int64_t n_steps, int32_t moments_every, 
     return PGC_OK;
 }
 
+// Time steps_per_candidate steps (no moments) under one launch configuration; +inf if the
+// configuration cannot run (tile not a multiple of the pass, more tiles than the scratch holds).
+static float time_launch(pgc_batch *b, const BatchLaunch &lc, int steps, pgc_status *st, cudaEvent_t e0, cudaEvent_t e1)
+{
+    if (b->run->set_launch(lc.block, lc.ppt, lc.g1_per_sm, lc.g2_per_sm) != cudaSuccess) return 1e30f;
+    if (lc.tile % b->run->pass() || lc.tile > 65535) return 1e30f;
+    if (b->run->set_tile(lc.tile, b->stream) != cudaSuccess) { cudaGetLastError(); return 1e30f; }
+    drop_graph(b);
+    cudaEventRecord(e0, b->stream);
+    *st = pgc_batch_step(b, steps, 0, 0);
+    cudaEventRecord(e1, b->stream);
+    if (*st != PGC_OK) return 1e30f;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
 pgc_status pgc_batch_autotune(pgc_batch *b, int32_t steps_per_candidate, int32_t *chosen_tile, double *ms_per_step)
 {
     if (!b) { g_batch_err = "batch is NULL"; return PGC_EINVAL; }
     if (steps_per_candidate < 1) return batch_fail(b, PGC_EINVAL, "steps_per_candidate < 1");
-    const int pass = b->run->pass();
-    std::vector<int> cand;
-    for (int t = pass; t <= 32768; t *= 2) cand.push_back(t);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = b->run->tile();
-    float best_ms = 1e30f;
-    const int every_saved = b->every;
+    // coordinate descent over the tile, the streaming block size, the particles per thread and
+    // the streaming and collider blocks per SM, from the current configuration, two rounds; the
+    // timed steps are part of the run (no configuration changes a trajectory)
+    BatchLaunch best = b->run->launch();
     pgc_status st = PGC_OK;
-    for (int t : cand) {
-        cudaError_t e = b->run->set_tile(t, b->stream);
-        if (e != cudaSuccess) continue;  // more tiles than the scratch holds
-        drop_graph(b);
-        cudaEventRecord(e0, b->stream);
-        st = pgc_batch_step(b, steps_per_candidate, 0, 0);
-        cudaEventRecord(e1, b->stream);
-        if (st != PGC_OK) break;
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = t; }
+    float best_ms = time_launch(b, best, steps_per_candidate, &st, e0, e1);
+    const int min_tile = (b->ctxs[0]->t.P <= 8) ? 1024 : 256;   // the scratch holds the tiles of this size
+    for (int round = 0; round < 2 && st == PGC_OK; ++round) {
+        for (int dim = 0; dim < 5 && st == PGC_OK; ++dim) {
+            std::vector<BatchLaunch> cand;
+            BatchLaunch c = best;
+            if (dim == 0) for (int t = min_tile; t <= 32768; t *= 2) { c.tile = t; cand.push_back(c); }
+            if (dim == 1) for (int blk : {128, 256}) { c.block = blk; c.g1_per_sm = std::max(1, b->run->max_g1(blk, c.ppt)); cand.push_back(c); }
+            if (dim == 2) for (int ppt : b->run->ppts()) { c.ppt = ppt; c.g1_per_sm = std::max(1, b->run->max_g1(c.block, ppt)); cand.push_back(c); }
+            if (dim == 3) for (int g = 1; g <= b->run->max_g1(c.block, c.ppt); ++g) { c.g1_per_sm = g; cand.push_back(c); }
+            if (dim == 4) for (int g = 2; g <= b->run->max_g2(); ++g) { c.g2_per_sm = g; cand.push_back(c); }
+            for (const BatchLaunch &x : cand) {
+                if (x.tile == best.tile && x.block == best.block && x.ppt == best.ppt && x.g1_per_sm == best.g1_per_sm &&
+                    x.g2_per_sm == best.g2_per_sm)
+                    continue;
+                const float ms = time_launch(b, x, steps_per_candidate, &st, e0, e1);
+                if (st != PGC_OK) break;
+                if (ms < best_ms) { best_ms = ms; best = x; }
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != PGC_OK) return st;
     drop_graph(b);
     b->every = -1;
-    (void)every_saved;
-    if (b->run->set_tile(best, b->stream) != cudaSuccess) return batch_fail(b, PGC_ECUDA, "set_tile");
-    if (chosen_tile) *chosen_tile = best;
+    if (b->run->set_launch(best.block, best.ppt, best.g1_per_sm, best.g2_per_sm) != cudaSuccess ||
+        b->run->set_tile(best.tile, b->stream) != cudaSuccess)
+        return batch_fail(b, PGC_ECUDA, "applying the chosen launch configuration");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[tune_key(b->ctxs)] = best;
+    }
+    if (chosen_tile) *chosen_tile = best.tile;
     if (ms_per_step) *ms_per_step = best_ms / steps_per_candidate;
+    return PGC_OK;
+}
+
+pgc_status pgc_batch_launch_config(const pgc_batch *b, int32_t *cfg5)
+{
+    if (!b || !cfg5) { g_batch_err = "NULL argument"; return PGC_EINVAL; }
+    const BatchLaunch l = b->run->launch();
+    cfg5[0] = l.tile;
+    cfg5[1] = l.block;
+    cfg5[2] = l.ppt;
+    cfg5[3] = l.g1_per_sm;
+    cfg5[4] = l.g2_per_sm;
     return PGC_OK;
 }
 

@@ -119,6 +119,41 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Warp sums of 16 values at once (a reduce-scatter): lane l ends with the sum over the 32 lanes
+// of v[(l >> 1) & 15] (lanes l and l ^ 1 hold the same sum), after 16 shuffles instead of the
+// 80 of 16 separate butterflies.  The lanes with l even add their sum, in FP64, to dst[(l >> 1)]
+// when that index is below count.
+__device__ __forceinline__ void warp_scatter16_add(const float v[16], double *dst, int count, int lane)
+{
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool up = lane & 16;
+        const float send = up ? v[j] : v[j + 8], keep = up ? v[j + 8] : v[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool up = lane & 8;
+        const float send = up ? a[j] : a[j + 4], keep = up ? a[j + 4] : a[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const bool up = lane & 4;
+        const float send = up ? a[j] : a[j + 2], keep = up ? a[j + 2] : a[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool up = lane & 2;
+        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    const int idx = (lane >> 1) & 15;
+    if (!(lane & 1) && idx < count) dst[idx] += (double)a[0];
+}
+
 // |k|^2 and the screen of the first flight time with an explicit operation order, so that
 // phase 1 and the continuation in phase 2 take bit-identical decisions.
 template <typename R>
@@ -288,6 +323,18 @@ __device__ __forceinline__ void observe(const Phys<R> &ph, R kx, R ky, R eps0, R
     e = eps;
 }
 
+// The same observables in FP32 from one reciprocal square root (rsqrtf, 2 ulp): 1/eps, eps and
+// both velocity components (the 36-node moment steps, where the divisions were the cost).
+__device__ __forceinline__ void observe_fast(const Phys<float> &ph, float kx, float ky, float eps0, float &vx, float &vy,
+                                             float &e)
+{
+    const float s2 = ph.hvF2 * (kx * kx + ky * ky) + eps0 * eps0;
+    const float inv = rsqrtf(s2);
+    vx = ph.hvF * kx * inv;
+    vy = ph.hvF * ky * inv;
+    e = s2 * inv;
+}
+
 // ------------------------------------------------------------------------------------------
 // Phase 1: every particle.  Each thread takes PPT consecutive particles and reads each
 // coefficient plane with one 16-byte load (float4 / 2 x double2); the ensemble is streamed once.
@@ -309,6 +356,12 @@ __device__ __forceinline__ void load_vec(const R *p, R v[PPT])
         const double2 a = reinterpret_cast<const double2 *>(p)[0];
         const double2 b = reinterpret_cast<const double2 *>(p)[1];
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else if constexpr (PPT == 2 && sizeof(R) == 4) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else if constexpr (PPT == 2 && sizeof(R) == 8) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x; v[1] = t.y;
     } else {
 #pragma unroll
         for (int e = 0; e < PPT; ++e) v[e] = p[e];
@@ -323,6 +376,10 @@ __device__ __forceinline__ void store_vec(R *p, const R v[PPT])
     } else if constexpr (PPT == 4 && sizeof(R) == 8) {
         reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    } else if constexpr (PPT == 2 && sizeof(R) == 4) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (PPT == 2 && sizeof(R) == 8) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
     } else {
 #pragma unroll
         for (int e = 0; e < PPT; ++e) p[e] = v[e];
@@ -345,12 +402,12 @@ struct P1Target {
 
 // One pass of a block over blockDim * PPT consecutive particles starting at i0 + threadIdx*PPT:
 // drift, reconstruction, flight-time screen, histogram (window or global), queue, moments.
-template <int P, int Q, typename R>
+// (PPT particles per thread; i0 a multiple of PPT.)
+template <int P, int Q, typename R, int PPT = Phase1PPT<P>::value>
 __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const P1Target<R> &t,
                                             int64_t i0, uint32_t *swin, int win_r0, bool use_win, bool out_step,
                                             double *smom_warp, unsigned int &oog)
 {
-    constexpr int PPT = Phase1PPT<P>::value;
     const int lane = threadIdx.x & 31;
     const int64_t NN = (int64_t)ph.Nk * ph.Nk;
     R cx[PPT][P], cy[PPT][P];
@@ -387,6 +444,7 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
                 }
             }
     }
+    constexpr bool kUnrollQ = P * Q <= 64 || TensorShape<P, Q>::value;
 #pragma unroll
     for (int e = 0; e < PPT; ++e) {
         const int64_t i = i0 + e;
@@ -405,7 +463,7 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
             maybe = screen_maybe(ph, nd, kkmax, r.x);
             if (!maybe) {
                 finished[e] = true;
-#pragma unroll ((P * Q <= 64 || TensorShape<P, Q>::value) ? Q : 1)
+#pragma unroll (kUnrollQ ? Q : 1)
                 for (int q = 0; q < Q; ++q) {
                     if (rl[q] < 0) { ++oog; continue; }
                     const int r = rl[q] >> 16, l = rl[q] & 0xffff;
@@ -431,24 +489,45 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
         }
     }
     if (out_step) {
-#pragma unroll 1
-        for (int q = 0; q < Q; ++q) {
-            R vx = (R)0, vy = (R)0, en = (R)0;
+        if constexpr (TensorShape<P, Q>::value && sizeof(R) == 4 && PPT == 1) {
+            // one particle per thread: the node values again by the (unrolled) sum factorisation,
+            // their observables streamed 16 at a time into warp reduce-scatters (node q,
+            // quantity j is value 3 q + j)
+            float buf[16];
+            const bool fin = finished[0];
+            recon_all(nd, cx[0], cy[0], [&](int q, R kx, R ky) {
+                float o[3] = {0.0f, 0.0f, 0.0f};
+                if (fin) observe_fast(ph, kx - nd.xs[q], ky, nd.eps0[q], o[0], o[1], o[2]);
 #pragma unroll
-            for (int e = 0; e < PPT; ++e)
-                if (finished[e]) {
-                    R kx, ky, a1, a2, a3;
-                    recon_node(nd, q, cx[e], cy[e], kx, ky);
-                    observe(ph, kx - nd.xs[q], ky, nd.eps0[q], a1, a2, a3);
-                    vx += a1; vy += a2; en += a3;
+                for (int j = 0; j < 3; ++j) {
+                    const int idx = 3 * q + j;
+                    buf[idx & 15] = o[j];
+                    if ((idx & 15) == 15 || idx == 3 * Q - 1) {
+                        for (int z = (idx & 15) + 1; z < 16; ++z) buf[z] = 0.0f;
+                        warp_scatter16_add(buf, smom_warp + (idx & ~15), (idx & 15) + 1, lane);
+                    }
                 }
-            vx = warp_sum(vx);
-            vy = warp_sum(vy);
-            en = warp_sum(en);
-            if (lane == 0) {
-                smom_warp[q * 3 + 0] += (double)vx;
-                smom_warp[q * 3 + 1] += (double)vy;
-                smom_warp[q * 3 + 2] += (double)en;
+            });
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < Q; ++q) {
+                R vx = (R)0, vy = (R)0, en = (R)0;
+#pragma unroll
+                for (int e = 0; e < PPT; ++e)
+                    if (finished[e]) {
+                        R kx, ky, a1, a2, a3;
+                        recon_node(nd, q, cx[e], cy[e], kx, ky);
+                        observe(ph, kx - nd.xs[q], ky, nd.eps0[q], a1, a2, a3);
+                        vx += a1; vy += a2; en += a3;
+                    }
+                vx = warp_sum(vx);
+                vy = warp_sum(vy);
+                en = warp_sum(en);
+                if (lane == 0) {
+                    smom_warp[q * 3 + 0] += (double)vx;
+                    smom_warp[q * 3 + 1] += (double)vy;
+                    smom_warp[q * 3 + 2] += (double)en;
+                }
             }
         }
     }
@@ -722,26 +801,30 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
     }
     R gc[NPL][6];  // rates of the current state at the lane's nodes (reused by the selection)
-    R tc = (R)0;
+    R tc = (R)0, Gt = (R)0;
     uint32_t c = 0;
-    bool touched = false;
+    bool touched = false, fresh = true;
     // One pass per free flight: majorant of the current state (Eq. (25)), flight time, and, if
     // the flight ends inside the step, a collision.  The rates and the random draw have one
-    // call site each (instruction-cache footprint).
+    // call site each (instruction-cache footprint).  An event that changes no node (self
+    // scattering or Pauli rejection everywhere) leaves the state, its rates and the majorant
+    // as they were: the projection of unchanged node values returns the same coefficients, so
+    // it, the reconstruction and the rates are not redone (fresh = false).
     for (;;) {
-        R gm = (R)0;
+        if (fresh) {
+            R gm = (R)0;
 #pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int q = r + s * G;
-            if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
+            }
+            Gt = ph.alpha1 * group_max<G>(gm, gmask);
         }
-        const R Gt = ph.alpha1 * group_max<G>(gm, gmask);
         const U4 rr = philox4x32_10((uint32_t)i, t.stream_id, t.step, c, t.key0, t.key1);
         const R dtc = (Gt > (R)0) ? -rlog<R>(u01<R>(rr.x)) / Gt : (R)INFINITY;
         if (!(tc + dtc < ph.dt)) break;             // group-uniform condition
         if ((int)c >= ph.max_coll) { if (r == 0) ++cnt.cap; break; }
         if (r == 0) ++cnt.att;
-        touched = true;
         EventAngles<R> ang;
         ang.reset(u01<R>(rr.w));
         const R target = u01<R>(rr.y) * Gt;
@@ -768,13 +851,17 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
             else ++cnt.rej;
         }
-        if (group_any<G>(changed, gmask) && r == 0) ++cnt.chg;
-        // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
-        project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, t.red);
+        fresh = group_any<G>(changed, gmask);
+        if (fresh && r == 0) ++cnt.chg;
+        if (fresh) {
+            touched = true;
+            // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
+            project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, t.red);
 #pragma unroll
-        for (int s = 0; s < NPL; ++s) {
-            const int q = r + s * G;
-            if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
+            }
         }
         tc += dtc;
         ++c;

@@ -93,6 +93,9 @@ public:
     // receives the block count
     virtual cudaError_t obs_at(const double *psi, const double *eps0, const double *xs, int nzc, double *part,
                                int *blocks, cudaStream_t s) = 0;
+    // reconstruction of the streaming kernel on the tensor cores (mode 1: FP16 hi/lo, three
+    // products; 2: one FP16 product); cudaErrorNotSupported where it is not compiled
+    virtual cudaError_t set_tc(int mode) { (void)mode; return cudaErrorNotSupported; }
 };
 
 // Factories, one per compiled (P, Q) shape; precision 0 = FP32, 1 = FP64.  nullptr if the

@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "pgc_kernels.cuh"
+#include "pgc_kernels_tc.cuh"
 #include "pgc_runner.h"
 
 namespace pgc {
@@ -15,7 +16,7 @@ namespace pgc {
 template <int P, int Q, typename R>
 class RunnerT final : public Runner {
 public:
-    RunnerT(const HostTables &t, const DevBuffers &b, int num_sms) : t_(t), b_(b)
+    RunnerT(const HostTables &t, const DevBuffers &b, int num_sms) : t_(t), b_(b), num_sms_(num_sms)
     {
         fill_phys(t);
         auto &nd = args_.nd;
@@ -166,9 +167,42 @@ public:
     {
         StepArgs<P, Q, R> a = args_at(n);
         a.out_step = out_step ? 1 : 0;
+        if constexpr (TensorShape<P, Q>::value && sizeof(R) == 4) {
+            if (tc_mode_) {
+                k_phase1_tc<P, Q><<<grid1_, kTcThreads, TcSmem<Q>::bytes, s>>>(a, tc_mode_);
+                count_launch();
+                return cudaGetLastError();
+            }
+        }
         k_phase1<P, Q, R><<<grid1_, kPhase1Threads, win_bytes_, s>>>(a);
         count_launch();
         return cudaGetLastError();
+    }
+
+    // The tensor-core streaming kernel: one CTA per SM (its shared memory admits no second
+    // one, which also keeps its 512 TMEM columns to itself), 4 tiles of 128 particles per CTA
+    // and iteration.  The phase-1 grid (and with it the moment partials of k_observe and
+    // k_finalize) becomes that kernel's grid.
+    cudaError_t set_tc(int mode) override
+    {
+        if constexpr (TensorShape<P, Q>::value && sizeof(R) == 4) {
+            if (mode == 0) return cudaSuccess;
+            if (mode != 1 && mode != 2) return cudaErrorInvalidValue;
+            cudaError_t e = cudaFuncSetAttribute(k_phase1_tc<P, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)TcSmem<Q>::bytes);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase1_tc<P, Q>, kTcThreads, TcSmem<Q>::bytes);
+            if (e != cudaSuccess) return e;
+            if (per_sm != 1) return cudaErrorNotSupported;   // TMEM is sized for one CTA per SM
+            const int64_t tiles = (b_.N + 127) / 128;
+            grid1_ = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kTcWG - 1) / kTcWG, num_sms_));
+            tc_mode_ = mode;
+            return cudaSuccess;
+        } else {
+            (void)mode;
+            return cudaErrorNotSupported;
+        }
     }
 
     cudaError_t phase2(int64_t n, bool out_step, cudaStream_t s) override
@@ -183,7 +217,7 @@ public:
     // the fused kernel takes two argument blocks: compiled where both fit the kernel-parameter
     // space (32764 bytes; all shapes but the 36-node FP64 one)
     static constexpr bool kFused = 2 * sizeof(StepArgs<P, Q, R>) + sizeof(int) <= 32764;
-    bool fused() const override { return kFused; }
+    bool fused() const override { return kFused && tc_mode_ == 0; }   // the fused kernel reconstructs on the FMA pipes
 
     // dynamic shared memory of the fused kernel: the phase-1 window, or the projection area of
     // its phase-2 blocks (ProjRed shapes), whichever is larger
@@ -321,6 +355,8 @@ private:
     size_t win_bytes_ = 0;
     int grid2_ = 1;
     int grid2f_ = 1;
+    int num_sms_ = 1;
+    int tc_mode_ = 0;
 };
 
 template <int P, int Q>

@@ -49,12 +49,13 @@ class pgc_config(C.Structure):
         ("seed", C.c_uint64), ("stream_id", C.c_uint32),
         ("precision", C.c_int32), ("pauli_norm", C.c_int32), ("final_state", C.c_int32),
         ("n_theta_edge", C.c_int32), ("max_collisions", C.c_int32), ("max_outputs", C.c_int32),
-        ("eps0_law", C.c_int32), ("width_nm", pgc_interval), ("splitting", C.c_int32),
+        ("eps0_law", C.c_int32), ("width_nm", pgc_interval), ("splitting", C.c_int32), ("tc_proj", C.c_int32),
     ]
 
 
 PGC_EPS0_AFFINE, PGC_EPS0_WIDTH = 0, 1
 PGC_SPLIT_LIE, PGC_SPLIT_STRANG = 0, 1
+PGC_TC_OFF, PGC_TC_F16X3, PGC_TC_F16 = 0, 1, 2
 
 
 _vp, _dp, _u32p, _u64p, _i64p = (C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint32),
@@ -86,6 +87,8 @@ SIGNATURES = {
     "pgc_batch_step": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32]),
     "pgc_batch_autotune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), _dp]),
     "pgc_batch_destroy": (None, [_vp]),
+    "pgc_window_objective": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int64, _dp]),
+    "pgc_batch_launch_config": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "pgc_batch_last_error": (C.c_char_p, [_vp]),
     "pgc_adjoint_query_sizes": (C.c_int, [_vp, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]),
     "pgc_adjoint": (C.c_int, [_vp, C.c_int64, C.c_int32, C.c_int32, C.c_int64, _dp, _vp, _dp, _dp]),
@@ -272,6 +275,14 @@ def pgc_batch_autotune(b, steps_per_candidate: int):
     return t.value, ms.value
 
 
+def pgc_batch_launch_config(b):
+    """(tile, threads per streaming block, particles per thread, streaming blocks per SM,
+    collider blocks per SM) of a batch."""
+    a = (C.c_int32 * 5)()
+    _check_batch(lib().pgc_batch_launch_config(_vp(b), a), _vp(b))
+    return dict(zip(["tile", "block", "ppt", "g1_per_sm", "g2_per_sm"], list(a)))
+
+
 def pgc_batch_destroy(b):
     if b:
         lib().pgc_batch_destroy(_vp(b))
@@ -337,6 +348,7 @@ def config_from(params: dict, max_outputs: int = 1024) -> pgc_config:
         c.width_nm.lo = p["W_lo"]
         c.width_nm.hi = p.get("W_hi", p["W_lo"])
     c.splitting = p.get("splitting", c.splitting)   # PGC_SPLIT_LIE (0) or PGC_SPLIT_STRANG (1)
+    c.tc_proj = p.get("tc_proj", c.tc_proj)         # PGC_TC_OFF (0), PGC_TC_F16X3 (1), PGC_TC_F16 (2)
     return c
 
 
@@ -454,6 +466,9 @@ class BatchSimulation:
     def autotune(self, steps_per_candidate: int = 3):
         return pgc_batch_autotune(self.batch, steps_per_candidate)
 
+    def launch_config(self):
+        return pgc_batch_launch_config(self.batch)
+
     def close(self):
         if getattr(self, "batch", None):
             pgc_batch_destroy(self.batch)
@@ -470,14 +485,13 @@ class BatchSimulation:
 
 def window_objective(params: dict, n_steps: int, moments_every: int, window_steps: int):
     """(Jbar, Vbar): averages over the moment records in (n_steps - window_steps, n_steps] of the
-    mean and the variance over z of the current J_x, from a plain run."""
+    mean and the variance over z of the current J_x, from a plain run (pgc_window_objective)."""
     sim = Simulation(params, max_outputs=n_steps // moments_every + 2)
-    sim.step(n_steps, moments_every)
-    m = sim.moments()
+    v = np.zeros(2)
+    _check(lib().pgc_window_objective(_vp(sim.ctx), int(n_steps), int(moments_every), int(window_steps), _ptr(v, _dp)),
+           _vp(sim.ctx))
     sim.close()
-    n = np.rint(m["t_fs"] / params["dt_fs"]).astype(np.int64)
-    sel = (n > n_steps - window_steps) & (n <= n_steps)
-    return float(m["mean"][sel, 3].mean()), float(m["var"][sel, 3].mean())
+    return float(v[0]), float(v[1])
 
 
 def adjoint(params: dict, n_steps: int, ckpt_every: int, moments_every: int, window_steps: int, weights=(1.0, 0.0)):
@@ -511,6 +525,7 @@ def _torch_function():
 
         @staticmethod
         def backward(fctx, grad_out):
+            # one adjoint sweep for the weights (dLoss/dJbar, dLoss/dVbar)
             p, n_steps, every, window, ckpt = fctx.cfg
             g = grad_out.detach().to("cpu", torch.float64).numpy()
             _, grad = adjoint(p, n_steps, ckpt, every, window, weights=g)

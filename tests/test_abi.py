@@ -8,6 +8,7 @@ import re
 import pytest
 
 from paper_2404_19602_gb300 import build, pgc
+from paper_2404_19602_gb300 import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -138,6 +139,29 @@ def test_splitting_field_is_checked(lib):
     assert e.value.status == pgc.PGC_EINVAL
     cfg.splitting = pgc.PGC_SPLIT_STRANG
     assert pgc.pgc_query_sizes(cfg)["P"] == 1
+
+
+def test_tensor_core_switch_is_checked(lib):
+    """tc_proj: an unknown value is invalid; the tensor-core reconstruction exists for the FP32
+    21 x 36 shape only."""
+    cfg = pgc.pgc_config_default()
+    assert cfg.tc_proj == pgc.PGC_TC_OFF
+    cfg.tc_proj = 3
+    with pytest.raises(pgc.PgcError) as e:
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EINVAL
+    cfg.tc_proj = pgc.PGC_TC_F16X3
+    with pytest.raises(pgc.PgcError) as e:        # the default shape is 1 x 1
+        pgc.pgc_query_sizes(cfg)
+    assert e.value.status == pgc.PGC_EUNSUPPORTED
+    for mode in (pgc.PGC_TC_F16X3, pgc.PGC_TC_F16):
+        c = pgc.config_from(W.scaled(W.GAP_FIELD_UQ_4E6, N=1000, tc_proj=mode))
+        s = pgc.pgc_query_sizes(c)
+        assert (s["P"], s["Q"]) == (21, 36)
+        c.precision = pgc.PGC_FP64
+        with pytest.raises(pgc.PgcError) as e:
+            pgc.pgc_query_sizes(c)
+        assert e.value.status == pgc.PGC_EUNSUPPORTED
 
 
 def test_plain_c_consumer_compiles_links_and_queries(lib, tmp_path):

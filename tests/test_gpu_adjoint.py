@@ -77,3 +77,23 @@ def test_autograd_function():
     (out[0] + 0.25 * out[1]).backward()
     _, g = pgc.adjoint(p, 40, 10, 5, 20, weights=[1.0, 0.25])
     assert np.allclose(theta.grad.numpy(), g, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("name", ["det", "gap"])
+def test_window_objective_equals_adjoint_value_and_oracle(name):
+    """pgc_window_objective (the objective without the gradient) equals the value pgc_adjoint
+    returns and the oracle's window average of the same run (FP64)."""
+    from paper_2404_19602_gb300 import pgc
+
+    p = CASES[name]
+    steps, every, window, ckpt = 60, 5, 30, 16
+    J, V = pgc.window_objective(p, steps, every, window)
+    val, _ = pgc.adjoint(p, steps, ckpt, every, window, weights=[1.0, 0.0])
+    # (the two runs group the FP64 moment partials differently; var_z of a deterministic input is
+    # rounding noise of ~1e-11 J^2)
+    assert abs(J - val[0]) <= 1e-12 * abs(val[0]) and abs(V - val[1]) <= 1e-9 * abs(val[1]) + 1e-9 * J ** 2
+    o = O.Oracle(p)
+    ref = o.window_objective(steps, every, window)
+    assert abs(J - ref[0]) <= 1e-9 * abs(ref[0])
+    # (a deterministic input has var_z = 0: the FP64 difference of squares leaves ~1e-11 J^2)
+    assert abs(V - ref[1]) <= 1e-7 * abs(ref[1]) + 1e-9 * ref[0] ** 2

@@ -65,21 +65,71 @@ def test_batch_cases_equal_standalone_runs(prec, use_graph):
     b.close()
 
 
-def test_batch_autotune_keeps_trajectories():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_cases_against_oracle(prec):
+    """Each case of an uneven batch (different fields and band-minimum intervals, ragged sizes)
+    against the FP64 CPU oracle run of that case alone (Algorithm 2 of Sec. 4.1 per case): in
+    FP64 the same decisions and states to rounding, in FP32 the moments within 1e-3."""
+    import oracle as O
     from paper_2404_19602_gb300 import pgc
 
-    cases = _cases("fp32")
-    b = pgc.BatchSimulation(cases, max_outputs=8)
-    tile, ms = b.autotune(2)
-    assert tile % 1024 == 0 and ms > 0
-    steps = sum(1 for t in range(1024, 32769) if t & (t - 1) == 0) * 2  # candidates x 2 steps
-    b.step(10, 0)
+    O.build()
+    cases = _cases(prec, ns=(2000, 3001, 777))
+    steps, every = 60, 10
+    b = pgc.BatchSimulation(cases, max_outputs=steps // every + 2, tile=1024)
+    b.step(steps, every)
     torch.cuda.synchronize()
     for p, sim in zip(cases, b.sims):
-        ks, _, hs, _ = _single(p, steps + 10, 0)
+        o = O.Oracle(p)
+        o.step(steps, every)
+        mb, mo = sim.moments(), o.moments()
+        assert np.allclose(mb["t_fs"], mo["t_fs"])
+        tol = 1e-9 if prec == "fp64" else 1e-3
+        for comp in (0, 2, 3):
+            for kind in ("mean", "var"):
+                a, r = mb[kind][:, comp], mo[kind][:, comp]
+                err = np.abs(a - r).max() / max(np.abs(r).max(), 1e-300)
+                assert err <= tol, (p["stream_id"], kind, comp, err)
+        g, r = sim.state(), o.state()
+        diverged = (np.abs(g - r).max(axis=(0, 1)) > (1e-9 if prec == "fp64" else 1e-4) * np.abs(r).max()).sum()
+        assert diverged <= (0 if prec == "fp64" else 2), diverged
+        if prec == "fp64":
+            cb, co = sim.counters(), o.counters()
+            assert cb["attempts"] == co["attempts"] and cb["rejected"] == co["rejected"]
+    b.close()
+
+
+@pytest.mark.parametrize("base", ["gap", "gap_field"])
+def test_batch_autotune_keeps_trajectories(base):
+    """The autotuner's candidates (tile, block size, particles per thread, both grids) advance the
+    cases; afterwards every case still equals its standalone run, the chosen configuration is a
+    valid one, and a later batch of the same kind starts from it."""
+    from paper_2404_19602_gb300 import pgc
+
+    if base == "gap":
+        cases = _cases("fp32")
+    else:   # two random inputs (21 coefficients on 6 x 6 nodes), uneven sizes
+        cases = [W.scaled(W.GAP_FIELD_UQ_4E6, N=n, Ex_lo=1000.0 + 1500.0 * c, Ex_hi=6000.0 + 1500.0 * c,
+                          stream_id=c, seed=7) for c, n in enumerate((3000, 5000, 1000, 7001))]
+    b = pgc.BatchSimulation(cases, max_outputs=8)
+    tile, ms = b.autotune(2)
+    lc = b.launch_config()
+    assert lc["tile"] == tile and ms > 0
+    assert lc["block"] in (128, 256) and lc["tile"] % (lc["block"] * lc["ppt"]) == 0
+    assert lc["ppt"] in ((4, 2, 1) if base == "gap" else (1,))
+    assert lc["g1_per_sm"] >= 1 and lc["g2_per_sm"] >= 2
+    b.step(10, 0)
+    torch.cuda.synchronize()
+    steps = b.sims[0].counters()["steps"]
+    for p, sim in zip(cases, b.sims):
+        assert sim.counters()["steps"] == steps
+        ks, _, hs, _ = _single(p, steps, 0)
         assert np.array_equal(sim.state(), ks)
         assert np.array_equal(sim.hist()[0], hs)
     b.close()
+    b2 = pgc.BatchSimulation(cases, max_outputs=8)       # tile 0: the cached choice
+    assert b2.launch_config() == lc
+    b2.close()
 
 
 def test_batch_two_random_inputs_fp64():
