@@ -291,9 +291,9 @@ k_finalize(const double *part1, const double *part2, const double *part3, const 
     const int t = threadIdx.x, col = t % n3, slot = t / n3;
     double s = 0.0;
     if (slot < nslot) {
-        for (int b = slot; b < f.g1; b += nslot) s += part1[(int64_t)b * n3 + col];
-        for (int b = slot; b < f.g2; b += nslot) s += part2[(int64_t)b * n3 + col];
-        for (int b = slot; b < f.g3; b += nslot) s += part3[(int64_t)b * n3 + col];
+        s = strided_sum(part1, slot, f.g1, nslot, n3, col, s);
+        s = strided_sum(part2, slot, f.g2, nslot, n3, col, s);
+        s = strided_sum(part3, slot, f.g3, nslot, n3, col, s);
     }
     red[t] = s;
     __syncthreads();
@@ -303,24 +303,99 @@ k_finalize(const double *part1, const double *part2, const double *part3, const 
         S[t] = acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // node values, one thread per node (FP64 divisions are slow on this part: in parallel), then
+    // the mean and variance over the nodes by one thread in node order
+    __shared__ double V[64 * 4];
+    if (t < f.Q) {
         const double qe = 1.602176634e-19;
+        const int q = t;
+        const double vx = S[q * 3 + 0] / f.N * f.vF_ms, vy = S[q * 3 + 1] / f.N * f.vF_ms;
+        const double en = S[q * 3 + 2] / f.N, jx = -qe * f.nq[q] * vx;
+        const double v[4] = {vx, vy, en, jx};
+        for (int o = 0; o < 4; ++o) {
+            V[q * 4 + o] = v[o];
+            rec[1 + q * 4 + o] = v[o];
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
         rec[0] = f.t_fs;
         double m[4] = {0, 0, 0, 0}, m2[4] = {0, 0, 0, 0};
-        for (int q = 0; q < f.Q; ++q) {
-            const double vx = S[q * 3 + 0] / f.N * f.vF_ms, vy = S[q * 3 + 1] / f.N * f.vF_ms;
-            const double en = S[q * 3 + 2] / f.N, jx = -qe * f.nq[q] * vx;
-            const double v[4] = {vx, vy, en, jx};
+        for (int q = 0; q < f.Q; ++q)
             for (int o = 0; o < 4; ++o) {
-                rec[1 + q * 4 + o] = v[o];
-                m[o] += f.w[q] * v[o];
-                m2[o] += f.w[q] * v[o] * v[o];
+                const double v = V[q * 4 + o];
+                m[o] += f.w[q] * v;
+                m2[o] += f.w[q] * v * v;
             }
-        }
         for (int o = 0; o < 4; ++o) {
             rec[1 + f.Q * 4 + o] = m[o];
             rec[1 + f.Q * 4 + 4 + o] = m2[o] - m[o] * m[o];
         }
+    }
+}
+
+// The record of a moment step over several SMs (the reduction is FP64, which this part issues at a
+// small fraction of its FP32 rate: one block would spend most of a step on it).  Block c sums
+// column c of the block partials (part1: g1 rows, part2: g2 rows, part3: g3 rows) with a
+// fixed-order tree and stores it in colsum[c]; the block that finishes last (its ticket from an
+// atomic counter is the last one; nothing waits) forms the record from the column sums as
+// k_finalize does and re-arms the counter.
+constexpr int kFinColThreads = 256;
+__global__ void __launch_bounds__(kFinColThreads)
+k_finalize_cols(const double *part1, const double *part2, const double *part3, const __grid_constant__ FinArgs f,
+                double *colsum, unsigned int *ticket, double *rec)
+{
+    __shared__ double red[kFinColThreads];
+    __shared__ double S[64 * 3];
+    __shared__ double V[64 * 4];
+    __shared__ bool last;
+    const int n3 = f.Q * 3, c = blockIdx.x, t = threadIdx.x;
+    double s = 0.0;
+    s = strided_sum(part1, t, f.g1, kFinColThreads, n3, c, s);
+    s = strided_sum(part2, t, f.g2, kFinColThreads, n3, c, s);
+    s = strided_sum(part3, t, f.g3, kFinColThreads, n3, c, s);
+    red[t] = s;
+    __syncthreads();
+    for (int w = kFinColThreads / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        colsum[c] = red[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned int)(n3 - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = t; j < n3; j += kFinColThreads) S[j] = __ldcg(colsum + j);
+    __syncthreads();
+    if (t < f.Q) {
+        const double qe = 1.602176634e-19;
+        const int q = t;
+        const double vx = S[q * 3 + 0] / f.N * f.vF_ms, vy = S[q * 3 + 1] / f.N * f.vF_ms;
+        const double en = S[q * 3 + 2] / f.N, jx = -qe * f.nq[q] * vx;
+        const double v[4] = {vx, vy, en, jx};
+        for (int o = 0; o < 4; ++o) {
+            V[q * 4 + o] = v[o];
+            rec[1 + q * 4 + o] = v[o];
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        rec[0] = f.t_fs;
+        double m[4] = {0, 0, 0, 0}, m2[4] = {0, 0, 0, 0};
+        for (int q = 0; q < f.Q; ++q)
+            for (int o = 0; o < 4; ++o) {
+                const double v = V[q * 4 + o];
+                m[o] += f.w[q] * v;
+                m2[o] += f.w[q] * v * v;
+            }
+        for (int o = 0; o < 4; ++o) {
+            rec[1 + f.Q * 4 + o] = m[o];
+            rec[1 + f.Q * 4 + 4 + o] = m2[o] - m[o] * m[o];
+        }
+        *ticket = 0u;
     }
 }
 
@@ -340,7 +415,7 @@ k_obs_fin(const double *part, const __grid_constant__ ObsFin f, double *out)
     const int t = threadIdx.x;
     if (t < kObsZ * 3) {
         double s = 0.0;
-        for (int b = 0; b < f.g; ++b) s += part[(int64_t)b * kObsZ * 3 + t];
+        s = strided_sum(part, 0, f.g, 1, kObsZ * 3, t, s);
         S[t] = s;
     }
     __syncthreads();
@@ -477,7 +552,7 @@ struct Layout {
     size_t state = 0, hist = 0, scratch = 0;
     size_t off_queue = 0, off_qcount = 0, off_counters = 0, off_nmax = 0, off_part1 = 0, off_part2 = 0,
            off_partN = 0, off_marks = 0, off_tables = 0, off_series = 0, off_recon = 0, off_tmpmax = 0,
-           off_obs = 0;
+           off_obs = 0, off_colsum = 0;
     int rec_len = 0;
 };
 }  // namespace
@@ -546,6 +621,7 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     L->off_recon = take((size_t)c->Nk * c->Nk * 4);
     L->off_tmpmax = take(4);
     L->off_obs = take((size_t)(kObsGrid * kObsZ * 3 + kObsZ * 4) * 8);
+    L->off_colsum = take((size_t)64 * 3 * 8);
     L->scratch = off;
     return PGC_OK;
 }
@@ -678,6 +754,7 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     ctx->tmp_max = (uint32_t *)(scr + L.off_tmpmax);
     ctx->obs_part = (double *)(scr + L.off_obs);
     ctx->obs_out = ctx->obs_part + (size_t)kObsGrid * kObsZ * 3;
+    ctx->colsum = (double *)(scr + L.off_colsum);
     ctx->rec_len = L.rec_len;
     ctx->run = make_runner(L.P, L.Q, cfg->precision, ctx->t, b, sms);
     if (!ctx->run) { delete ctx; return fail(nullptr, PGC_EUNSUPPORTED, "no kernel for this shape"); }
@@ -749,8 +826,8 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
         f.g2 = g2;
         f.g3 = g3;
         const double *p3 = g3 > 0 ? ctx->b.partN + (n & 1) * (int64_t)kGrid2Max * Q3 : nullptr;
-        k_finalize<<<1, kFinThreads, 0, s>>>(ctx->b.part1 + (n & 1) * ctx->b.part1_stride, ctx->b.part2, p3, f,
-                                             ctx->series + ctx->T_out * ctx->rec_len);
+        k_finalize_cols<<<Q3, kFinColThreads, 0, s>>>(ctx->b.part1 + (n & 1) * ctx->b.part1_stride, ctx->b.part2, p3, f,
+                                                      ctx->colsum, ctx->b.qcount + 3, ctx->series + ctx->T_out * ctx->rec_len);
         count_launch();
         ctx->T_out++;
     };

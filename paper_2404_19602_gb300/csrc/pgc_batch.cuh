@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kPhase1Threads)
 k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
 {
     constexpr int NW = kPhase1Threads / 32;
-    __shared__ double smom[NW][Q * 3];
+    __shared__ typename MomAcc<R>::T smom[NW][Q * 3];
     __shared__ int64_t stile[kBatchMaxCases + 1];
     __shared__ __align__(16) uint32_t snd[(sizeof(Nodes<P, Q, R>) + 3) / 4];
     extern __shared__ uint32_t swin[];
@@ -105,7 +105,7 @@ k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
         if (a.use_win)
             for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) swin[j] = 0u;
         if (out)
-            for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
+            for (int j = lane; j < Q * 3; j += 32) acc_zero(smom[warp][j]);
         // this tile's share of clearing the case's buffer of step n+2
         {
             const int64_t t = tile - cd.tile0;
@@ -134,7 +134,7 @@ k_phase1_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
         if (out)
             for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
                 double s = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += smom[w][j];   // fixed order
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += acc_value(smom[w][j]);   // fixed order
                 a.part_tiles[tile * (Q * 3) + j] = s;
             }
         oog = warp_sum(oog);
@@ -219,8 +219,7 @@ k_finalize_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
     const int nslot = 256 / n3;
     const int t = threadIdx.x, col = t % n3, slot = t / n3;
     double s = 0.0;
-    if (slot < nslot)
-        for (int64_t b = cd.tile0 + slot; b < cd.tile0 + cd.ntiles; b += nslot) s += a.part_tiles[b * n3 + col];
+    if (slot < nslot) s = strided_sum(a.part_tiles, cd.tile0 + slot, cd.tile0 + cd.ntiles, nslot, n3, col, s);
     red[t] = s;
     __syncthreads();
     if (t < n3) {
@@ -231,21 +230,30 @@ k_finalize_batch(const __grid_constant__ BatchArgs<P, Q, R> a)
         S[t] = acc;
     }
     __syncthreads();
-    if (t == 0) {
+    // node values, one thread per node, then the mean and variance by one thread in node order
+    __shared__ double V[Q * 4];
+    double *rec = cd.series + (*cd.t_out) * a.rec_len;
+    if (t < Q) {
         const double qe = 1.602176634e-19;
-        double *rec = cd.series + (*cd.t_out) * a.rec_len;
+        const int q = t;
+        const double vx = S[q * 3 + 0] / (double)cd.N * a.vF_ms, vy = S[q * 3 + 1] / (double)cd.N * a.vF_ms;
+        const double en = S[q * 3 + 2] / (double)cd.N, jx = -qe * cd.nq[q] * vx;
+        const double v[4] = {vx, vy, en, jx};
+        for (int o = 0; o < 4; ++o) {
+            V[q * 4 + o] = v[o];
+            rec[1 + q * 4 + o] = v[o];
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
         rec[0] = (double)step * (double)a.ph.dt;
         double m[4] = {0, 0, 0, 0}, m2[4] = {0, 0, 0, 0};
-        for (int q = 0; q < Q; ++q) {
-            const double vx = S[q * 3 + 0] / (double)cd.N * a.vF_ms, vy = S[q * 3 + 1] / (double)cd.N * a.vF_ms;
-            const double en = S[q * 3 + 2] / (double)cd.N, jx = -qe * cd.nq[q] * vx;
-            const double v[4] = {vx, vy, en, jx};
+        for (int q = 0; q < Q; ++q)
             for (int o = 0; o < 4; ++o) {
-                rec[1 + q * 4 + o] = v[o];
-                m[o] += cd.w[q] * v[o];
-                m2[o] += cd.w[q] * v[o] * v[o];
+                const double v = V[q * 4 + o];
+                m[o] += cd.w[q] * v;
+                m2[o] += cd.w[q] * v * v;
             }
-        }
         for (int o = 0; o < 4; ++o) {
             rec[1 + Q * 4 + o] = m[o];
             rec[1 + Q * 4 + 4 + o] = m2[o] - m[o] * m[o];

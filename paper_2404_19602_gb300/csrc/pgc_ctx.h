@@ -20,6 +20,7 @@ struct pgc_ctx {
     int rec_len = 0;
     double *series = nullptr;
     uint32_t *tmp_max = nullptr;
+    double *colsum = nullptr;    // [64 * 3] column sums of k_finalize_cols
     double *obs_part = nullptr;  // [kObsGrid][kObsZ][3] block partials of pgc_observe_at
     double *obs_out = nullptr;   // [kObsZ][4]
     bool failed = false;

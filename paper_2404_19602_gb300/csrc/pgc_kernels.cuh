@@ -119,11 +119,33 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Per-warp moment accumulators of the streaming kernels.  FP64 in the FP64 mode.  In the FP32
+// mode a float-float pair (hi, lo) advanced by the error-free transformation TwoSum (Knuth,
+// TAOCP vol. 2, 4.2.2): hi + lo carries ~48 significant bits, and no operation runs on the FP64
+// pipe, which on this part issues a small fraction of the FP32 rate.  The block's partial sum
+// is then formed in FP64 from hi + lo, in a fixed warp order.
+template <typename R> struct MomAcc;
+template <> struct MomAcc<double> { using T = double; };
+template <> struct MomAcc<float> { using T = float2; };
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(float2 &a) { a = make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ void acc_add(double &a, double x) { a += x; }
+__device__ __forceinline__ void acc_add(float2 &a, float x)
+{
+    const float s = a.x + x;
+    const float bp = s - a.x;
+    const float err = (a.x - (s - bp)) + (x - bp);
+    a.x = s;
+    a.y += err;
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(float2 a) { return (double)a.x + (double)a.y; }
+
 // Warp sums of 16 values at once (a reduce-scatter): lane l ends with the sum over the 32 lanes
 // of v[(l >> 1) & 15] (lanes l and l ^ 1 hold the same sum), after 16 shuffles instead of the
-// 80 of 16 separate butterflies.  The lanes with l even add their sum, in FP64, to dst[(l >> 1)]
-// when that index is below count.
-__device__ __forceinline__ void warp_scatter16_add(const float v[16], double *dst, int count, int lane)
+// 80 of 16 separate butterflies.  The lanes with l even add their sum to the accumulator
+// dst[(l >> 1)] when that index is below count.
+__device__ __forceinline__ void warp_scatter16_add(const float v[16], float2 *dst, int count, int lane)
 {
     float a[8];
 #pragma unroll
@@ -151,7 +173,49 @@ __device__ __forceinline__ void warp_scatter16_add(const float v[16], double *ds
     }
     a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
     const int idx = (lane >> 1) & 15;
-    if (!(lane & 1) && idx < count) dst[idx] += (double)a[0];
+    if (!(lane & 1) && idx < count) acc_add(dst[idx], a[0]);
+}
+
+// s + p[b * n3 + col] summed over b = b0, b0 + step, ... < b1 in that order (the fixed-order
+// reductions of the block partials).  The loads are issued eight at a time ahead of their adds,
+// so a thread waits for one memory round trip per eight rows instead of one per row; the sum is
+// the plain loop's, bit for bit.
+__device__ __forceinline__ double strided_sum(const double *p, int64_t b0, int64_t b1, int step, int n3, int col, double s)
+{
+    for (int64_t b = b0; b < b1; b += 8 * (int64_t)step) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t bb = b + (int64_t)k * step;
+            v[k] = bb < b1 ? p[bb * n3 + col] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (b + (int64_t)k * step < b1) s += v[k];
+    }
+    return s;
+}
+
+// The same for 4 values: lane l ends with the sum over the 32 lanes of v[(l >> 3) & 3]; lanes
+// 0, 8, 16, 24 add their sum to the accumulator dst[l >> 3] when that index is below count.
+__device__ __forceinline__ void warp_scatter4_add(const float v[4], float2 *dst, int count, int lane)
+{
+    float a[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const bool up = lane & 16;
+        const float send = up ? v[j] : v[j + 2], keep = up ? v[j + 2] : v[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    {
+        const bool up = lane & 8;
+        const float send = up ? a[0] : a[1], keep = up ? a[1] : a[0];
+        a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+    const int idx = (lane >> 3) & 3;
+    if (!(lane & 7) && idx < count) acc_add(dst[idx], a[0]);
 }
 
 // |k|^2 and the screen of the first flight time with an explicit operation order, so that
@@ -406,7 +470,7 @@ struct P1Target {
 template <int P, int Q, typename R, int PPT = Phase1PPT<P>::value>
 __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q, R> &nd, const P1Target<R> &t,
                                             int64_t i0, uint32_t *swin, int win_r0, bool use_win, bool out_step,
-                                            double *smom_warp, unsigned int &oog)
+                                            typename MomAcc<R>::T *smom_warp, unsigned int &oog)
 {
     const int lane = threadIdx.x & 31;
     const int64_t NN = (int64_t)ph.Nk * ph.Nk;
@@ -508,6 +572,22 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
                     }
                 }
             });
+        } else if constexpr (sizeof(R) == 4) {
+            // per node: the three observables summed over the thread's particles, then one 4-value
+            // warp reduce-scatter (6 shuffles instead of the 15 of three butterflies)
+#pragma unroll 1
+            for (int q = 0; q < Q; ++q) {
+                float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int e = 0; e < PPT; ++e)
+                    if (finished[e]) {
+                        float kx, ky, a1, a2, a3;
+                        recon_node(nd, q, cx[e], cy[e], kx, ky);
+                        observe(ph, kx - nd.xs[q], ky, nd.eps0[q], a1, a2, a3);
+                        s[0] += a1; s[1] += a2; s[2] += a3;
+                    }
+                warp_scatter4_add(s, smom_warp + q * 3, 3, lane);
+            }
         } else {
 #pragma unroll 1
             for (int q = 0; q < Q; ++q) {
@@ -524,9 +604,9 @@ __device__ __forceinline__ void phase1_pass(const Phys<R> &ph, const Nodes<P, Q,
                 vy = warp_sum(vy);
                 en = warp_sum(en);
                 if (lane == 0) {
-                    smom_warp[q * 3 + 0] += (double)vx;
-                    smom_warp[q * 3 + 1] += (double)vy;
-                    smom_warp[q * 3 + 2] += (double)en;
+                    acc_add(smom_warp[q * 3 + 0], vx);
+                    acc_add(smom_warp[q * 3 + 1], vy);
+                    acc_add(smom_warp[q * 3 + 2], en);
                 }
             }
         }
@@ -557,13 +637,13 @@ __device__ __forceinline__ void phase1_block(const StepArgs<P, Q, R> &a, int bid
 {
     constexpr int PPT = Phase1PPT<P>::value;
     constexpr int NW = kPhase1Threads / 32;
-    __shared__ double smom[NW][Q * 3];
+    __shared__ typename MomAcc<R>::T smom[NW][Q * 3];
     __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.use_win)
         for (int j = threadIdx.x; j < Q * kWinWords; j += blockDim.x) swin[j] = 0u;
     if (a.out_step)
-        for (int j = lane; j < Q * 3; j += 32) smom[warp][j] = 0.0;
+        for (int j = lane; j < Q * 3; j += 32) acc_zero(smom[warp][j]);
     __syncthreads();
 
     // housekeeping for the next steps
@@ -633,7 +713,7 @@ __device__ __forceinline__ void phase1_block(const StepArgs<P, Q, R> &a, int bid
         for (int j = threadIdx.x; j < Q * 3; j += blockDim.x) {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) s += smom[w][j];
+            for (int w = 0; w < NW; ++w) s += acc_value(smom[w][j]);
             a.part1[(int64_t)bid * (Q * 3) + j] = s;
         }
     }
@@ -657,9 +737,13 @@ k_phase1(const __grid_constant__ StepArgs<P, Q, R> a)
 #ifndef PGC_GROUP36
 #define PGC_GROUP36 32
 #endif
+#ifndef PGC_GROUP8
+#define PGC_GROUP8 8
+#endif
+
 template <int Q> struct GroupOf {
     static constexpr int G = (Q == 36) ? PGC_GROUP36
-                           : (Q >= 32) ? 32 : (Q > 16 ? 32 : (Q > 8 ? 16 : (Q > 4 ? 8 : (Q > 2 ? 4 : (Q > 1 ? 2 : 1)))));
+                           : (Q >= 32) ? 32 : (Q > 16 ? 32 : (Q > 8 ? 16 : (Q > 4 ? PGC_GROUP8 : (Q > 2 ? 4 : (Q > 1 ? 2 : 1)))));
     static constexpr int NPL = (Q + G - 1) / G;  // nodes per lane
 };
 

@@ -90,7 +90,7 @@ k_phase1_tc(const __grid_constant__ StepArgs<P, Q, float> a, int mode)
     uint32_t *swin = reinterpret_cast<uint32_t *>(smem);
     unsigned char *sA = smem + S::offA;
     unsigned char *sB = smem + S::offB;
-    double *smom = reinterpret_cast<double *>(smem + S::offMom);
+    float2 *smom = reinterpret_cast<float2 *>(smem + S::offMom);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + S::offBar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + S::offBar + 8 * kTcWG);
 
@@ -103,7 +103,7 @@ k_phase1_tc(const __grid_constant__ StepArgs<P, Q, float> a, int mode)
     // --- set-up: window, moment partials, operands (zero padding), B = scaled Psi split ---
     if (a.use_win)
         for (int j = tid; j < Q * kWinWords; j += kTcThreads) swin[j] = 0u;
-    for (int j = tid; j < (kTcThreads / 32) * Q * 3; j += kTcThreads) smom[j] = 0.0;
+    for (int j = tid; j < (kTcThreads / 32) * Q * 3; j += kTcThreads) acc_zero(smom[j]);
     for (int j = tid; j < kTcWG * 4 * kTcOpBytes / 16; j += kTcThreads)
         reinterpret_cast<uint4 *>(sA)[j] = make_uint4(0u, 0u, 0u, 0u);
     for (int j = tid; j < kTcN * kTcK / 2; j += kTcThreads) {
@@ -149,7 +149,7 @@ k_phase1_tc(const __grid_constant__ StepArgs<P, Q, float> a, int mode)
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lanes
     const uint32_t idesc = umma_idesc_f16(128, kTcN);
     unsigned char *opA = sA + (size_t)wg * 4 * kTcOpBytes;               // x_hi, x_lo, y_hi, y_lo
-    double *smw = smom + warp * (Q * 3);
+    float2 *smw = smom + warp * (Q * 3);
 
     const int64_t ntiles = (a.N + 127) / 128;
     const int64_t stride = (int64_t)nb * kTcWG;
@@ -354,7 +354,7 @@ k_phase1_tc(const __grid_constant__ StepArgs<P, Q, float> a, int mode)
         for (int j = tid; j < Q * 3; j += kTcThreads) {
             double s = 0.0;
 #pragma unroll
-            for (int w = 0; w < kTcThreads / 32; ++w) s += smom[w * (Q * 3) + j];
+            for (int w = 0; w < kTcThreads / 32; ++w) s += acc_value(smom[w * (Q * 3) + j]);
             a.part1[(int64_t)bid * (Q * 3) + j] = s;
         }
     tc_fence_after();

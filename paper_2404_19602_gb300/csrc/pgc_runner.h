@@ -46,7 +46,8 @@ struct DevBuffers {
     int64_t hist_stride = 0;        // elements per buffer (>= Q*Nk*Nk, multiple of 64)
     uint32_t *queue = nullptr;      // [2][queue_stride] (queue_stride 0: one queue for both slots)
     int64_t queue_stride = 0;
-    uint32_t *qcount = nullptr;     // [8]: collider counters n % 3 in [0, 3), phase-1 tile counters n % 3 in [4, 7)
+    uint32_t *qcount = nullptr;     // [8]: collider counters n % 3 in [0, 3), phase-1 tile counters n % 3 in [4, 7),
+                                    // [3] the ticket counter of k_finalize_cols
     unsigned long long *counters = nullptr;  // [8]
     uint32_t *nmax = nullptr;       // [Q]
     double *part1 = nullptr;        // [2][kMaxGrid1][Q*3] (part1_stride 0: one slot)
