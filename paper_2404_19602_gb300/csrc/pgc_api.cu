@@ -612,9 +612,9 @@ static pgc_status check_config(const pgc_config *c, Layout *L, std::string *msg)
     L->off_qcount = take(8 * 4);
     L->off_counters = take(8 * 8);
     L->off_nmax = take((size_t)L->Q * 4);
-    L->off_part1 = take((size_t)2 * kMaxGrid1 * L->Q * 3 * 8);
-    L->off_part2 = take((size_t)kGrid2Max * L->Q * 3 * 8);
-    L->off_partN = take((size_t)2 * kGrid2Max * L->Q * 3 * 8);
+    L->off_part1 = take((size_t)kPartSlots * kMaxGrid1 * L->Q * 3 * 8);
+    L->off_part2 = take((size_t)kPartSlots * kGrid2Max * L->Q * 3 * 8);
+    L->off_partN = take((size_t)kPartSlots * kGrid2Max * L->Q * 3 * 8);
     L->off_marks = take((size_t)kMarkSlots * L->mark_words * 4);
     L->off_tables = take(kTableBytes);
     L->off_series = take((size_t)c->max_outputs * L->rec_len * 8);
@@ -742,6 +742,7 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     b.part1 = (double *)(scr + L.off_part1);
     b.part1_stride = (int64_t)kMaxGrid1 * L.Q * 3;
     b.part2 = (double *)(scr + L.off_part2);
+    b.part2_stride = (int64_t)kGrid2Max * L.Q * 3;
     b.partN = (double *)(scr + L.off_partN);
     b.marks = (uint32_t *)(scr + L.off_marks);
     b.mark_words = L.mark_words;
@@ -794,6 +795,23 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
     return PGC_OK;
 }
 
+static_assert(sizeof(pgc_ctx::fin_done) / sizeof(cudaEvent_t) == pgc::kPartSlots, "one event per partial-sum slot");
+
+// The second stream (highest priority) and events of the pipelined records, created on first use.
+static cudaError_t fin_stream_of(pgc_ctx *ctx)
+{
+    if (ctx->fin_stream) return cudaSuccess;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fin_ready, cudaEventDisableTiming);
+    for (int k = 0; k < pgc::kPartSlots && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&ctx->fin_done[k], cudaEventDisableTiming);
+    cudaStream_t fs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&fs, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) ctx->fin_stream = fs;
+    return e;
+}
+
 pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
 {
     if (!ctx) return fail(nullptr, PGC_EINVAL, "ctx is NULL");
@@ -821,13 +839,16 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
     // record of step n: phase-1 partials of step n (g1 blocks), phase-2 partials of step n (g2
     // blocks) and, when phase 2 of step n - 1 carried particles into step n, its partials of step
     // n (g3 blocks)
-    auto finalize = [&](int64_t n, int g2, int g3) {
+    // the record of step n from the partials of its slot, on stream fs
+    auto finalize = [&](int64_t n, int g2, int g3, cudaStream_t fs) {
         f.t_fs = (n + 1) * ctx->t.dt;
         f.g2 = g2;
         f.g3 = g3;
-        const double *p3 = g3 > 0 ? ctx->b.partN + (n & 1) * (int64_t)kGrid2Max * Q3 : nullptr;
-        k_finalize_cols<<<Q3, kFinColThreads, 0, s>>>(ctx->b.part1 + (n & 1) * ctx->b.part1_stride, ctx->b.part2, p3, f,
-                                                      ctx->colsum, ctx->b.qcount + 3, ctx->series + ctx->T_out * ctx->rec_len);
+        const int64_t slot = n % kPartSlots;
+        const double *p3 = g3 > 0 ? ctx->b.partN + slot * (int64_t)kGrid2Max * Q3 : nullptr;
+        k_finalize_cols<<<Q3, kFinColThreads, 0, fs>>>(ctx->b.part1 + slot * ctx->b.part1_stride,
+                                                       ctx->b.part2 + slot * ctx->b.part2_stride, p3, f, ctx->colsum,
+                                                       ctx->b.qcount + 3, ctx->series + ctx->T_out * ctx->rec_len);
         count_launch();
         ctx->T_out++;
     };
@@ -851,16 +872,38 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
     const int64_t n0 = ctx->step;
     const int g2 = ctx->run->grid2(), g2f = ctx->run->grid2f();
     cudaError_t e = cudaSuccess;
-    if (!ctx->pipeline || n_steps < 2) {
+    // The records are reduced on a second stream of the highest priority, beside the next step
+    // launches: the record of step m (slot m % kPartSlots) is queued there behind the launch that
+    // completes it, and the first launch that overwrites that slot (step m + 3) waits for it.  The
+    // call ends by joining that stream, so that the caller's stream orders everything it did.
+    bool pending[kPartSlots] = {false, false, false};
+    if (moments_every > 0 && n_steps > 0) e = fin_stream_of(ctx);
+    const cudaStream_t fs = ctx->fin_stream;
+    auto finalize_async = [&](int64_t m, int g2v, int g3v) {
+        cudaError_t r = cudaEventRecord(ctx->fin_ready, s);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(fs, ctx->fin_ready, 0);
+        if (r != cudaSuccess) return r;
+        finalize(m, g2v, g3v, fs);
+        pending[m % kPartSlots] = true;
+        return cudaEventRecord(ctx->fin_done[m % kPartSlots], fs);
+    };
+    auto before_writing = [&](int64_t k) {   // a launch that overwrites the partials of slot k % kPartSlots
+        const int sl = (int)(k % kPartSlots);
+        if (!pending[sl]) return cudaSuccess;
+        pending[sl] = false;
+        return cudaStreamWaitEvent(s, ctx->fin_done[sl], 0);
+    };
+    if (e == cudaSuccess && (!ctx->pipeline || n_steps < 2)) {
         for (int64_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
             const int64_t n = n0 + k;
             hist_max(n);
             cudaEvent_t *ev = nullptr;
             if ((e = prof_slot(n, &ev)) != cudaSuccess) break;
+            if ((e = before_writing(n)) != cudaSuccess) break;
             e = ctx->run->step(n, is_out(n), s, ev);
-            if (e == cudaSuccess && is_out(n)) finalize(n, g2, 0);
+            if (e == cudaSuccess && is_out(n)) e = finalize_async(n, g2, 0);
         }
-    } else {
+    } else if (e == cudaSuccess) {
         // Pipelined form: phase 1 of step n0, then one fused launch per step n (phase 1 of n
         // beside phase 2 of n - 1, which carries its particles into step n), then phase 2 of the
         // last step, so that the call ends on a step boundary.  The record of step n - 1 is
@@ -876,17 +919,24 @@ pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every)
             hist_max(n - 1);
             cudaEvent_t *ev = nullptr;
             if ((e = prof_slot(n, &ev)) != cudaSuccess) break;
+            if ((e = before_writing(n)) != cudaSuccess) break;
             if (ev) cudaEventRecord(ev[0], s);
             e = ctx->run->step_fused(n, is_out(n), is_out(n - 1), s);
             if (ev) for (int j = 1; j < 4; ++j) cudaEventRecord(ev[j], s);
-            if (e == cudaSuccess && is_out(n - 1)) finalize(n - 1, g2f, n - 1 > n0 ? g2f : 0);
+            if (e == cudaSuccess && is_out(n - 1)) e = finalize_async(n - 1, g2f, n - 1 > n0 ? g2f : 0);
         }
         if (e == cudaSuccess) {
             hist_max(n1);
-            e = ctx->run->phase2(n1, is_out(n1), s);
-            if (e == cudaSuccess && is_out(n1)) finalize(n1, g2, n1 > n0 ? g2f : 0);
+            e = before_writing(n1);
+            if (e == cudaSuccess) e = ctx->run->phase2(n1, is_out(n1), s);
+            if (e == cudaSuccess && is_out(n1)) e = finalize_async(n1, g2, n1 > n0 ? g2f : 0);
         }
     }
+    for (int sl = 0; sl < kPartSlots; ++sl)
+        if (pending[sl]) {
+            cudaError_t r = cudaStreamWaitEvent(s, ctx->fin_done[sl], 0);
+            if (e == cudaSuccess) e = r;
+        }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step");
     ctx->step = n0 + n_steps;
@@ -1171,6 +1221,10 @@ void pgc_destroy(pgc_ctx *ctx)
     if (!ctx) return;
     for (auto &ev : ctx->prof_ev) cudaEventDestroy(ev);
     if (ctx->prof_ref) cudaEventDestroy(ctx->prof_ref);
+    if (ctx->fin_stream) cudaStreamDestroy(ctx->fin_stream);
+    if (ctx->fin_ready) cudaEventDestroy(ctx->fin_ready);
+    for (auto &ev : ctx->fin_done)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx->run;
     delete ctx;

@@ -21,6 +21,10 @@ struct pgc_ctx {
     double *series = nullptr;
     uint32_t *tmp_max = nullptr;
     double *colsum = nullptr;    // [64 * 3] column sums of k_finalize_cols
+    // records of pipelined steps: reduced on a second stream (created on first use)
+    cudaStream_t fin_stream = nullptr;
+    cudaEvent_t fin_ready = nullptr;
+    cudaEvent_t fin_done[3] = {nullptr, nullptr, nullptr};   // by partial-sum slot
     double *obs_part = nullptr;  // [kObsGrid][kObsZ][3] block partials of pgc_observe_at
     double *obs_out = nullptr;   // [kObsZ][4]
     bool failed = false;

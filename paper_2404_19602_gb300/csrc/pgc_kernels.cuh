@@ -45,6 +45,10 @@ constexpr int kWinWords = kWin * kWin / 2;
 // partials: n % 2; collider bitmaps: n % 3.
 constexpr int kHistBufs = 4;
 constexpr int kQSlots = 3;
+// Moment partial sums of step n (streaming part1, collider part2, carried partN) live in slot
+// n % kPartSlots: the record of step m is reduced beside the launches of steps m + 1 and m + 2,
+// and step m + 3 is the first to overwrite its slot.
+constexpr int kPartSlots = 3;
 constexpr int kMarkSlots = 3;
 
 // Basis of total degree <= 5 in two variables on 6 x 6 tensor nodes (the compiled 2-D shape):

@@ -50,10 +50,11 @@ struct DevBuffers {
                                     // [3] the ticket counter of k_finalize_cols
     unsigned long long *counters = nullptr;  // [8]
     uint32_t *nmax = nullptr;       // [Q]
-    double *part1 = nullptr;        // [2][kMaxGrid1][Q*3] (part1_stride 0: one slot)
+    double *part1 = nullptr;        // [kPartSlots][kMaxGrid1][Q*3] (part1_stride 0: one slot)
     int64_t part1_stride = 0;
-    double *part2 = nullptr;        // [kGrid2Max][Q*3]
-    double *partN = nullptr;        // [2][kGrid2Max][Q*3] or nullptr (pipelined steps only)
+    double *part2 = nullptr;        // [kPartSlots][kGrid2Max][Q*3] (part2_stride 0: one slot)
+    int64_t part2_stride = 0;
+    double *partN = nullptr;        // [kPartSlots][kGrid2Max][Q*3] or nullptr (pipelined steps only)
     uint32_t *marks = nullptr;      // [kMarkSlots][mark_words] collider bitmaps or nullptr (pipelined steps only)
     int64_t mark_words = 0;
     void *tables = nullptr;         // device copy of the node tables (kTableBytes) or nullptr

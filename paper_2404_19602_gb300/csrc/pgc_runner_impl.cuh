@@ -157,8 +157,9 @@ public:
         a.mark_next = M(n + 1);
         a.mark_clear = M(n + 1);
         a.skip = nullptr;
-        a.part1 = b_.part1 + (n & 1) * b_.part1_stride;
-        a.partN = b_.partN ? b_.partN + ((n + 1) & 1) * (int64_t)kGrid2Max * Q * 3 : nullptr;
+        a.part1 = b_.part1 + (n % kPartSlots) * b_.part1_stride;
+        a.part2 = b_.part2 + (n % kPartSlots) * b_.part2_stride;
+        a.partN = b_.partN ? b_.partN + ((n + 1) % kPartSlots) * (int64_t)kGrid2Max * Q * 3 : nullptr;
         a.step = (uint32_t)n;
         return a;
     }
