@@ -751,6 +751,26 @@ template <int Q> struct GroupOf {
     static constexpr int NPL = (Q + G - 1) / G;  // nodes per lane
 };
 
+// Node slots of a lane (s = 0 .. NPL - 1) read and written with a runtime slot index by selects,
+// so that a rolled loop over the slots keeps the per-slot arrays in registers: the per-node code
+// of the collision loop is emitted once instead of NPL times (instruction-cache footprint).
+template <int N, typename T>
+__device__ __forceinline__ T slot_get(const T (&a)[N], int s)
+{
+    T v = a[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k)
+        if (s == k) v = a[k];
+    return v;
+}
+template <int N, typename T>
+__device__ __forceinline__ void slot_set(T (&a)[N], int s, T v)
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (s == k) a[k] = v;
+}
+
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v, unsigned mask)
 {
@@ -883,11 +903,24 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         cx[h] = t.khat[(int64_t)h * t.ld + i];
         cy[h] = t.khat[(int64_t)(P + h) * t.ld + i];
     }
-#pragma unroll
-    for (int s = 0; s < NPL; ++s) {
-        const int q = r + s * G;
-        if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
-    }
+    // the node values of the lane's slots from the coefficients
+    // (NPL > 1: loops over the slots are rolled, see slot_get)
+    auto recon_slots = [&](const R (&ccx)[P], const R (&ccy)[P], R (&x)[NPL], R (&y)[NPL]) {
+        if constexpr (NPL > 1) {
+#pragma unroll 1
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q >= Q) break;
+                R a, b;
+                recon_node(nd, q, ccx, ccy, a, b);
+                slot_set(x, s, a);
+                slot_set(y, s, b);
+            }
+        } else {
+            recon_node(nd, r, ccx, ccy, x[0], y[0]);
+        }
+    };
+    recon_slots(cx, cy, kx, ky);
     R gc[NPL][6];  // rates of the current state at the lane's nodes (reused by the selection)
     R tc = (R)0, Gt = (R)0;
     uint32_t c = 0;
@@ -901,10 +934,25 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
     for (;;) {
         if (fresh) {
             R gm = (R)0;
+            if constexpr (NPL > 1) {
+#pragma unroll 1
+                for (int s = 0; s < NPL; ++s) {
+                    const int q = r + s * G;
+                    if (q >= Q) break;
+                    R g[6];
+                    gm = fmax(gm, rates6(ph, slot_get(kx, s), slot_get(ky, s), nd.eps0[q], g));
 #pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
+                    for (int m = 0; m < 6; ++m)
+#pragma unroll
+                        for (int k = 0; k < NPL; ++k)
+                            if (s == k) gc[k][m] = g[m];
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const int q = r + s * G;
+                    if (q < Q) gm = fmax(gm, rates6(ph, kx[s], ky[s], nd.eps0[q], gc[s]));
+                }
             }
             Gt = ph.alpha1 * group_max<G>(gm, gmask);
         }
@@ -917,6 +965,39 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
         ang.reset(u01<R>(rr.w));
         const R target = u01<R>(rr.y) * Gt;
         bool changed = false;
+        if constexpr (NPL > 1) {
+#pragma unroll 1
+            for (int s = 0; s < NPL; ++s) {
+                const int q = r + s * G;
+                if (q >= Q) break;
+                int l = 6;
+                R cum = (R)0;
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    R gsm = gc[0][m];
+#pragma unroll
+                    for (int k = 1; k < NPL; ++k)
+                        if (s == k) gsm = gc[k][m];
+                    cum += gsm;
+                    if (l == 6 && target < cum) l = m;
+                }
+                if (l == 6) continue;  // self scattering: h^7 = identity
+                R nkx, nky;
+                final_state(ph, l, slot_get(kx, s), slot_get(ky, s), nd.eps0[q], ang, &nkx, &nky);
+                bool accept = true;
+                if (ph.pauli_mode != 2) {
+                    const int cl = cell_of(ph, nd.lkx[q], nkx + nd.dq[q], nky);
+                    if (cl >= 0) accept = pauli_accept(t.Hcur[(int64_t)q * NN + cl], t.nmax[q], rr.z);
+                }
+                if (accept) {
+                    slot_set(kx, s, nkx);
+                    slot_set(ky, s, nky);
+                    changed = true;
+                } else {
+                    ++cnt.rej;
+                }
+            }
+        } else {
 #pragma unroll
         for (int s = 0; s < NPL; ++s) {
             const int q = r + s * G;
@@ -939,17 +1020,14 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             if (accept) { kx[s] = nkx; ky[s] = nky; changed = true; }
             else ++cnt.rej;
         }
+        }
         fresh = group_any<G>(changed, gmask);
         if (fresh && r == 0) ++cnt.chg;
         if (fresh) {
             touched = true;
             // collisional matrices K1 + K2 (Eqs. (28)-(30)): project the node values
             project_group<P, Q, R>(nd, kx, ky, r, gmask, cx, cy, t.red);
-#pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                const int q = r + s * G;
-                if (q < Q) recon_node(nd, q, cx, cy, kx[s], ky[s]);
-            }
+            recon_slots(cx, cy, kx, ky);
         }
         tc += dtc;
         ++c;
@@ -970,19 +1048,30 @@ __device__ __forceinline__ void collide_particle(const Phys<R> &ph, const Nodes<
             t.khat[(int64_t)(P + h) * t.ld + i] = vy;
         }
     }
-#pragma unroll
-    for (int s = 0; s < NPL; ++s) {
-        const int q = r + s * G;
-        if (q >= Q) continue;
-        const int cl = cell_of(ph, nd.lkx[q], kx[s], ky[s]);
+    auto finish_node = [&](int q, R x, R y) {
+        const int cl = cell_of(ph, nd.lkx[q], x, y);
         if (cl >= 0) atomicAdd(&t.Hnext[(int64_t)q * NN + cl], 1u);
         else ++cnt.oog;
         if (t.out_step) {
             R vx, vy, e;
-            observe(ph, kx[s] - nd.xs[q], ky[s], nd.eps0[q], vx, vy, e);
+            observe(ph, x - nd.xs[q], y, nd.eps0[q], vx, vy, e);
             atomicAdd(&t.mom[q * 3 + 0], (double)vx);
             atomicAdd(&t.mom[q * 3 + 1], (double)vy);
             atomicAdd(&t.mom[q * 3 + 2], (double)e);
+        }
+    };
+    if constexpr (NPL > 1) {
+#pragma unroll 1
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q >= Q) break;
+            finish_node(q, slot_get(kx, s), slot_get(ky, s));
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < NPL; ++s) {
+            const int q = r + s * G;
+            if (q < Q) finish_node(q, kx[s], ky[s]);
         }
     }
     if constexpr (EXT) {
