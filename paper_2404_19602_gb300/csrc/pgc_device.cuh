@@ -223,7 +223,7 @@ __device__ __forceinline__ R rate_bound(const Phys<R> &ph, R eps, R eps0max)
 // ------------------------------------------------------------------------------------------
 // Angle laws of the final states (Sec. 3).  One uniform u per collision, shared by all nodes.
 // (1 + cos th) on [0, 2pi): solve th + sin th = 2 pi u ; (1 - cos th): th - sin th = 2 pi u.
-// Both maps are monotone; bisection to the working precision.
+// Both maps are monotone; safeguarded Newton iteration to the working precision.
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __device__ __noinline__ R solve_angle(R u, R sgn)

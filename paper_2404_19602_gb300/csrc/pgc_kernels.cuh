@@ -30,9 +30,9 @@ constexpr int kPhase1Threads = 256;
 constexpr int kPhase2Threads = 128;
 constexpr int kMaxGrid1 = 4096;   // block partials sized for at most this many phase-1 blocks
 constexpr int kGrid2 = 608;       // phase-2 blocks (grid-stride over the queue)
-// The large shapes (P * Q > 64: many nodes per collision chain, ~20 chains per group in sequence)
-// run five phase-2 blocks per SM, one more wave of latency-bound chains in flight.
-template <int P, int Q> struct Phase2Blocks { static constexpr int per_sm = (P * Q > 64) ? 5 : 4; };
+// Phase-2 blocks per SM the collider kernel is compiled for (four: no spills at 36 nodes; five
+// were measured 1 % slower with the collider's rolled slot loops, six slower still).
+template <int P, int Q> struct Phase2Blocks { static constexpr int per_sm = 4; };
 constexpr int kGrid2Max = 5 * 152; // phase-2 partial sums are sized for this many blocks
 // Block-private histogram window of phase 1: kWin x kWin cells per node around the grid centre,
 // 16-bit counts packed two per 32-bit word in shared memory, flushed to the global histogram once
