@@ -96,16 +96,29 @@ template <> __device__ __forceinline__ double rfloor<double>(double x) { return 
 
 // ------------------------------------------------------------------------------------------
 // Cell of a wave-vector on the fixed grid [-Lk, Lk]^2 (Sec. 3); -1 outside.  The FP64 mode
-// divides (as the definition reads); the FP32 mode multiplies by the reciprocal.
+// gives the cell of the division (as the definition reads, floor_div_f64); the FP32 mode
+// multiplies by the reciprocal.
 // ------------------------------------------------------------------------------------------
+// floor(fl(x / dk)) in FP64 with the division taken only where it can matter: x * fl(1/dk) lies
+// within 2 ulps of fl(x / dk), so their floors differ only if an integer lies within 2 ulps of
+// the product; there (8 ulps, to spare) the quotient is formed by the division itself.  The FP64
+// divide is a long sequence on the FP64 pipe, which this part issues at a small fraction of the
+// FP32 rate; the cell is the same as the division's in every case.
+__device__ __forceinline__ int floor_div_f64(double x, double dk, double inv_dk)
+{
+    const double y = x * inv_dk;
+    if (fabs(y - rint(y)) <= fabs(y) * 0x1p-49) return __double2int_rd(x / dk);
+    return __double2int_rd(y);
+}
+
 template <typename R>
 __device__ __forceinline__ bool cell_rl(const Phys<R> &ph, R kx, R ky, int &r, int &l)
 {
     // floor and conversion in one rounding-down conversion; outside the grid (including the
     // saturated conversions of huge values) fails the unsigned comparison
     if constexpr (sizeof(R) == 8) {
-        r = __double2int_rd((kx + ph.Lk) / ph.dk);
-        l = __double2int_rd((ky + ph.Lk) / ph.dk);
+        r = floor_div_f64(kx + ph.Lk, ph.dk, ph.inv_dk);
+        l = floor_div_f64(ky + ph.Lk, ph.dk, ph.inv_dk);
     } else {
         r = __float2int_rd((kx + ph.Lk) * ph.inv_dk);
         l = __float2int_rd((ky + ph.Lk) * ph.inv_dk);
@@ -127,8 +140,8 @@ template <typename R>
 __device__ __forceinline__ bool cell_rl(const Phys<R> &ph, R lkx, R kx, R ky, int &r, int &l)
 {
     if constexpr (sizeof(R) == 8) {
-        r = __double2int_rd((kx + lkx) / ph.dk);
-        l = __double2int_rd((ky + ph.Lk) / ph.dk);
+        r = floor_div_f64(kx + lkx, ph.dk, ph.inv_dk);
+        l = floor_div_f64(ky + ph.Lk, ph.dk, ph.inv_dk);
     } else {
         r = __float2int_rd((kx + lkx) * ph.inv_dk);
         l = __float2int_rd((ky + ph.Lk) * ph.inv_dk);
