@@ -54,3 +54,29 @@ def test_traffic_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
     assert bench._traffic("k_step", "gap_uq") is None
     assert bench._traffic("no_such_kernel", "gap_uq") is None
     assert bench.throughput(1000, 2, 10, 5, 11.0) == 1000 * 2 * 10 * 5 / 11e-3
+
+
+def test_parity_errors_are_normwise_over_the_shared_output_times():
+    """The `parity` key's errors: max over the first n output times of |a - b|, divided by the
+    largest |b| over those times, per quantity (J_x, V_x, energy) and moment (mean, var)."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    T = 6
+    b = {"mean": np.zeros((T, 4)), "var": np.zeros((T, 4))}
+    b["mean"][:, 3] = np.linspace(1.0, 2.0, T)          # J_x: 1.0 ... 2.0, largest |b| of the first 5 is 1.8
+    b["mean"][:, 0] = -np.linspace(3.0, 4.0, T)         # V_x
+    b["mean"][:, 2] = 5.0
+    b["var"][:, 3] = 0.5
+    a = {k: v.copy() for k, v in b.items()}
+    a["mean"][2, 3] += 0.018                            # J_x off by 0.018 at one time: 0.01 of 1.8
+    a["mean"][T - 1, 0] += 0.4                          # V_x off beyond the compared times
+    a["var"][:, 3] *= 1.1                               # var J_x 10 % off everywhere
+    e = bench._moment_errors(a, b, T - 1)
+    assert abs(e["mean_Jx"] - 0.01) < 1e-12
+    assert e["mean_Vx"] == 0.0                          # only the first n = T - 1 times count
+    assert abs(e["var_Jx"] - 0.1) < 1e-12
+    assert e["mean_energy"] == 0.0 and e["var_Vx"] == 0.0 and e["var_energy"] == 0.0   # zero reference: 0
+    assert set(e) == {"%s_%s" % (k, q) for k in ("mean", "var") for q in ("Jx", "Vx", "energy")}
