@@ -186,7 +186,12 @@ pgc_status pgc_init(const pgc_config *cfg, void *d_state, void *d_hist, void *d_
  * pgc_set_pipeline) one launch per step n runs the streaming work of step n beside the collider
  * work of step n - 1, whose particles are carried on through the drift and screen of step n
  * (the streaming work skips them).  Trajectories, histograms and counters are the same in both
- * forms; moment sums may differ in the last bits (FP32 summation order). */
+ * forms; moment sums may differ in the last bits (FP32 summation order).
+ * With moments_every > 0 the moment records (Sec. 4.2) are reduced on a second stream of the
+ * highest priority, beside the following step launches; the context creates it on the first
+ * such call and pgc_destroy releases it.  Before it returns, the call makes the context's stream
+ * wait for that stream (event waits, no host synchronisation), so work queued on the context's
+ * stream after the call is ordered after everything the call did. */
 pgc_status pgc_step(pgc_ctx *ctx, int64_t n_steps, int32_t moments_every);
 
 /* Switch the pipelined form of pgc_step on (1) or off (0).  Available for every compiled shape
